@@ -1,0 +1,161 @@
+"""The oracle: a plain CPU implementation of the checkerboard Metropolis sweep
+of the 2D Ising and Blume-Capel models and of its per-sweep observables.
+
+TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` may import this
+package.  The product library never calls it, and it never imports the
+product package.  Everything it computes is in ``isg_oracle.c``; this module
+only marshals numpy arrays into that C code.
+
+Parity status of each function (what pins it is in ``tests/test_oracle_*``):
+  philox4x32_10   pinned: black-box agreement with cuRAND's host Philox4_32_10
+  threshold       pinned: closed-form error bound, beta = 0 / infinity limits
+  init_random     pinned: T = infinity statistics (spin balance, 1/3 split)
+  run (sweeps)    pinned: exact enumeration (Ising L=4, Blume-Capel L=3, 4),
+                  Kaufman's exact finite-L energy at beta_c, Onsager / Yang
+                  off-critical, acceptance frequencies, beta = 0 and
+                  beta = infinity limits, global spin-flip symmetry
+  measure         pinned: invariants and closed forms on constructed lattices
+  xi2             pinned: closed forms on constructed row/column sums
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ISING = 0
+BLUME_CAPEL = 1
+
+_lib = None
+
+
+def lib():
+    """Load (building first if needed) the oracle shared library."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        u32p = ctypes.POINTER(ctypes.c_uint32)
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        i8p = ctypes.POINTER(ctypes.c_int8)
+        f64p = ctypes.POINTER(ctypes.c_double)
+        L.oracle_philox4x32_10.argtypes = [u32p, u32p, u32p]
+        L.oracle_philox4x32_10.restype = None
+        L.oracle_site_random.argtypes = [ctypes.c_uint64, ctypes.c_uint64,
+                                         ctypes.c_uint32, ctypes.c_uint32]
+        L.oracle_site_random.restype = ctypes.c_uint32
+        L.oracle_threshold.argtypes = [ctypes.c_double, ctypes.c_double, ctypes.c_int]
+        L.oracle_threshold.restype = ctypes.c_uint64
+        L.oracle_bc_proposal.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.oracle_bc_proposal.restype = ctypes.c_int
+        L.oracle_init_random.argtypes = [i8p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64]
+        L.oracle_init_random.restype = ctypes.c_int
+        L.oracle_measure.argtypes = [i8p, ctypes.c_int64, i64p, i32p, i32p]
+        L.oracle_measure.restype = ctypes.c_int
+        L.oracle_run.argtypes = [i8p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
+                                 ctypes.c_uint64, ctypes.c_int64, f64p, ctypes.c_double,
+                                 ctypes.c_int64, i64p, i32p, i32p, ctypes.c_int, ctypes.c_int]
+        L.oracle_run.restype = ctypes.c_int64
+        L.oracle_xi2.argtypes = [ctypes.c_int64, ctypes.c_int64, i64p, i32p, i32p]
+        L.oracle_xi2.restype = ctypes.c_double
+        _lib = L
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def default_threads() -> int:
+    return max(1, len(os.sched_getaffinity(0)))
+
+
+def philox4x32_10(ctr, key):
+    """Philox4x32-10 of one 4-word counter and 2-word key -> 4 words."""
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    lib().oracle_philox4x32_10(c, k, o)
+    return [int(v) for v in o]
+
+
+def site_random(seed: int, j: int, w2: int, w3: int) -> int:
+    """Random word of same-colour index j for counter words (w2, w3)."""
+    return int(lib().oracle_site_random(seed & (2**64 - 1), j, w2 & 0xFFFFFFFF,
+                                        w3 & 0xFFFFFFFF))
+
+
+def threshold(beta: float, dE: float, bits: int) -> int:
+    """rne(2^bits exp(-beta dE)) for dE > 0; 2^bits (always accept) for dE <= 0."""
+    return int(lib().oracle_threshold(float(beta), float(dE), int(bits)))
+
+
+def bc_proposal(s: int, b: int) -> int:
+    return int(lib().oracle_bc_proposal(int(s), int(b)))
+
+
+def init_random(L: int, model: int, seed: int) -> np.ndarray:
+    """Hot start: an L x L int8 lattice drawn from the beta = 0 measure."""
+    s = np.zeros((L, L), dtype=np.int8)
+    rc = lib().oracle_init_random(_ptr(s, ctypes.c_int8), L, model, seed & (2**64 - 1))
+    if rc != 0:
+        raise ValueError("oracle_init_random rejected its arguments")
+    return s
+
+
+def measure(s: np.ndarray):
+    """(B, M, Q, R[L], C[L]) of a lattice; energy per spin = (-B + Delta Q)/L^2."""
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    L = s.shape[0]
+    bmq = np.zeros(3, dtype=np.int64)
+    R = np.zeros(L, dtype=np.int32)
+    C = np.zeros(L, dtype=np.int32)
+    rc = lib().oracle_measure(_ptr(s, ctypes.c_int8), L, _ptr(bmq, ctypes.c_int64),
+                              _ptr(R, ctypes.c_int32), _ptr(C, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError("oracle_measure rejected its arguments")
+    return int(bmq[0]), int(bmq[1]), int(bmq[2]), R, C
+
+
+def run(s: np.ndarray, model: int, seed: int, t0: int, betas, delta: float = 0.0,
+        record_every: int = 0, with_rows: bool = True, nthreads: int = 1,
+        sequential: bool = False):
+    """Advance lattice ``s`` in place by len(betas) sweeps t0, t0+1, ...
+
+    Returns (bmq[nrec,3], R[nrec,L], C[nrec,L]) of the recorded sweeps (R and
+    C are None when with_rows is False).
+    """
+    assert s.dtype == np.int8 and s.flags.c_contiguous and s.shape[0] == s.shape[1]
+    L = s.shape[0]
+    betas = np.ascontiguousarray(np.asarray(betas, dtype=np.float64).reshape(-1))
+    n = betas.size
+    nrec_max = n // record_every if record_every > 0 else 0
+    bmq = np.zeros((max(nrec_max, 1), 3), dtype=np.int64)
+    R = C = None
+    Rp = Cp = ctypes.POINTER(ctypes.c_int32)()
+    if with_rows and nrec_max > 0:
+        R = np.zeros((nrec_max, L), dtype=np.int32)
+        C = np.zeros((nrec_max, L), dtype=np.int32)
+        Rp, Cp = _ptr(R, ctypes.c_int32), _ptr(C, ctypes.c_int32)
+    nrec = lib().oracle_run(_ptr(s, ctypes.c_int8), L, model, seed & (2**64 - 1), t0, n,
+                            _ptr(betas, ctypes.c_double), float(delta), record_every,
+                            _ptr(bmq, ctypes.c_int64), Rp, Cp, int(nthreads),
+                            int(bool(sequential)))
+    if nrec < 0:
+        raise ValueError("oracle_run rejected its arguments")
+    return bmq[:nrec], (R[:nrec] if R is not None else None), (C[:nrec] if C is not None else None)
+
+
+def xi2(M, R, C) -> float:
+    """Ensemble second-moment correlation length from n replicas' M, R, C."""
+    M = np.ascontiguousarray(np.asarray(M, dtype=np.int64).reshape(-1))
+    R = np.ascontiguousarray(np.asarray(R, dtype=np.int32))
+    C = np.ascontiguousarray(np.asarray(C, dtype=np.int32))
+    n = M.size
+    L = R.size // max(n, 1)
+    assert R.size == n * L and C.size == n * L
+    return float(lib().oracle_xi2(n, L, _ptr(M, ctypes.c_int64), _ptr(R, ctypes.c_int32),
+                                  _ptr(C, ctypes.c_int32)))
