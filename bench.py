@@ -1,0 +1,309 @@
+#!/usr/bin/env python
+"""Throughput of the checkerboard Metropolis sweep on one B300 (or N replicas).
+
+A step is one pass of the whole hot path over the workload: the host
+threshold table for beta(t), the colour-0 and colour-1 half-sweeps, and the
+observables (B, M, Q, row and column sums) recorded on the device.  The
+default workload is the single large Ising lattice, L = 2^20 (2^40 spins,
+128 GiB of bit-planes), hot start, quench to beta_c; the lattice is far larger
+than L2, so no flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload ising_large|blume_capel_large|ising_small|blume_capel_parity]
+
+Prints one JSON line.  `value` is the device-timed throughput (spin-flip
+attempts per ns, all ranks); `e2e` is the same metric through the public C
+ABI with host inputs (the beta of each sweep) and host outputs (each sweep's
+record read back, xi_2 computed on the host) inside the timed region.
+With --impl reference the oracle (CPU) is timed on a bounded sample.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2503_14688_b300 import workloads as wl  # noqa: E402
+
+METRIC = "spin flips/ns per B300 (Ising, BC) & % roofline; batched/served vs single lattice"
+UNIT = "flips/ns"
+
+# Algorithmic integer operations per site update (roofline):
+# Philox4x32-10 per 4 sites = 20 wide multiplies + 20 three-input XORs;
+# the acceptance compares: Ising 2 per site, Blume-Capel 1 per site plus the
+# proposal bit.  Units: one 32-lane-issue integer operation.
+ALG_OPS_PER_SITE = {wl.ISING: 10.0 + 2.0, wl.BLUME_CAPEL: 10.0 + 2.0}
+SMS = 148
+INT_LANES_PER_SM = 128     # 4 SMSPs x 32 lanes, one warp-instruction per SMSP per clock
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        return p.get("sm_max_mhz", 2032.0), "measured sm_max_mhz"
+    return 2032.0, "fallback (recipe max SM clock)"
+
+
+def _workload(name):
+    return {"ising_large": wl.ising_large, "blume_capel_large": wl.blume_capel_large,
+            "ising_small": wl.ising_quench_small,
+            "blume_capel_parity": wl.blume_capel_parity}[name]()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.out = os.path.join("/tmp", "isg_clocks_%d.csv" % os.getpid())
+
+    def start(self):
+        try:
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.out):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.remove(self.out)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(model, beta, delta, budget_s=12.0, seed=wl.BASE_SEED + 99):
+    """The oracle, as it stands, on the host cores: a bounded sample of the
+    workload (an L = 4096 lattice; the per-site rate of the byte-per-site
+    oracle does not depend on L once out of cache)."""
+    import oracle
+
+    threads = oracle.default_threads()
+    L = 4096
+    s = oracle.init_random(L, model, seed)
+    t0 = time.perf_counter()
+    oracle.run(s, model, seed, 0, [beta], delta=delta, nthreads=threads)
+    one = time.perf_counter() - t0
+    n = max(1, min(2000, int(budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.run(s, model, seed, 1, [beta] * n, delta=delta, record_every=n, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": L * L * n / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{'Ising' if model == 0 else 'Blume-Capel'} L={L} hot start, {n} sweeps "
+                      f"at the workload's beta with the observables of the last sweep, "
+                      f"{dt:.1f} s on {threads} threads"}
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+
+    threads = oracle.default_threads()
+    L = 4096
+    seed = w.seed
+    s = oracle.init_random(L, w.model, seed)
+    for i in range(args.warmup):
+        oracle.run(s, w.model, seed, i, [w.beta], delta=w.delta, nthreads=threads)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run(s, w.model, seed, args.warmup + i, [w.beta], delta=w.delta, record_every=1,
+                   nthreads=threads)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = L * L * args.steps / total / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": w.name, "sample_L": L, "note": "oracle on host cores, one "
+                       "sweep of an L=4096 sample of the same model/beta per step"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"L={L}, {args.steps} sweeps"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, w):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import paper_2503_14688_b300 as P
+
+    stream = torch.cuda.Stream()
+    seed = w.seed + rank  # replicas: independent lattices, one per rank
+    lat = P.Lattice(w.L, w.model, seed=seed, delta=w.delta, stream=stream,
+                    record_capacity=args.steps + args.warmup + 4)
+    lat.init_random()
+    beta = w.beta
+
+    def step(events=None):
+        if events is not None:
+            events[0].record(stream)
+        lat.half_sweep(0, beta)
+        if events is not None:
+            events[1].record(stream)
+        lat.half_sweep(1, beta)
+        if events is not None:
+            events[2].record(stream)
+        lat.record()
+
+    for _ in range(args.warmup):
+        step()
+    lat.read_records(with_sums=False)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    start.record(stream)
+    for i in range(args.steps):
+        step(evs[i])
+    stop.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist:
+        dist.barrier()
+    ms = start.elapsed_time(stop)
+    half0 = [e[0].elapsed_time(e[1]) for e in evs]
+    half1 = [e[1].elapsed_time(e[2]) for e in evs]
+    recs = lat.read_records()
+    assert len(recs) == args.steps
+    xi = P.xi2([recs[-1].M], recs[-1].R[None], recs[-1].C[None])
+
+    # end to end through the C ABI: host beta in, host record out, xi_2 on host
+    e2e_steps = max(2, min(args.steps, 5))
+    betas_host = np.full(1, beta)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lat.sweep(1, betas=betas_host, record_every=1)
+        r = lat.read_records()[0]
+        P.xi2([r.M], r.R[None], r.C[None])
+    e2e_s = time.perf_counter() - t0
+
+    ms_t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms, e2e_s = float(ms_t[0]), float(ms_t[1])
+    sites = float(w.L) * float(w.L)
+    value = world * sites * args.steps / (ms * 1e6)
+    e2e_value = world * sites * e2e_steps / (e2e_s * 1e9)
+
+    sm_max, peak_src = _peaks()
+    peak = SMS * INT_LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s
+    dom = half1 if statistics.mean(half1) >= statistics.mean(half0) else half0
+    dom_ms = statistics.mean(dom)
+    ops = ALG_OPS_PER_SITE[w.model] * sites / 2
+    achieved = ops / (dom_ms * 1e-3) / 1e12
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic (hot-start lattice from the seeded Philox)",
+            "config": {"workload": w.name, "model": "ising" if w.model == 0 else "blume_capel",
+                       "L": w.L, "spins": int(sites), "beta": beta, "delta": w.delta,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2_flush": "not needed: lattice %.0f GiB >> 126 MB L2"
+                                   % (P.Lattice.nbytes(w.model, w.L) / 2**30),
+                       "step": "host thresholds + half-sweep colour 0 + half-sweep colour 1 "
+                               "+ on-device record of B, M, Q, row and column sums"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "half-sweep colour %d" % (1 if dom is half1 else 0),
+                         "ops_per_site": ALG_OPS_PER_SITE[w.model],
+                         "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int lanes x "
+                                       f"{sm_max:.0f} MHz ({peak_src})",
+                         "half_sweep_ms": [statistics.mean(half0), statistics.mean(half1)]},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8,
+                    "d2h_bytes_per_step": 32 + 8 * w.L, "steps": e2e_steps},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clk,
+            "xi2_last": xi,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(w.model, beta, w.delta)
+        print(json.dumps(line), flush=True)
+    lat.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ising_large")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--L", type=int, default=0, help="override the workload's L (profiling)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    w = _workload(args.workload)
+    if args.L:
+        w.L = args.L
+        w.name = f"{w.name}@L={args.L}"
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,201 @@
+/*
+ * isg.h -- C ABI of libisg: the checkerboard single-spin-flip Metropolis sweep
+ * of the 2D spin-1/2 Ising and spin-1 Blume-Capel models on an L x L periodic
+ * square lattice, on one NVIDIA B300 (sm_103a), with the per-sweep
+ * observables behind the energy, the magnetisation and the second-moment
+ * correlation length.
+ *
+ * Model (Eq. (1) of arXiv 2503.14688):
+ *     H = -J sum_<xy> s_x s_y + Delta sum_x s_x^2,   J = 1,
+ *     s in {-1,+1} (Ising) or {-1,0,+1} (Blume-Capel).
+ * Dynamics (Introduction; Table I): Metropolis, made parallel by a
+ * checkerboard decomposition; the unit of time is one full-lattice sweep.
+ * Random numbers (Appendix B): 32-bit integers, here Philox4x32-10 keyed per
+ * site, so every accept/reject is an integer comparison and every result is
+ * reproducible bit for bit.
+ *
+ * Conventions used by every call:
+ *   - Site (x, y), x, y in [0, L); colour c = (x + y) & 1; same-colour index
+ *     j = (y*L + x) >> 1.  Sweep t updates colour 0, then colour 1, both with
+ *     the inverse temperature beta(t).
+ *   - Random word of a site at sweep t: word (j & 3) of Philox4x32-10 with
+ *     key (lo32(seed), hi32(seed)) and counter (lo32(j>>2), hi32(j>>2), t, c).
+ *     The hot start uses the counter (lo32(j>>2), hi32(j>>2), 0, c | 2).
+ *   - Acceptance of a move with energy change dE: always if dE <= 0; else
+ *     Ising iff u < rne(2^32 exp(-beta dE)), Blume-Capel iff
+ *     (u >> 1) < rne(2^31 exp(-beta dE)), with the thresholds computed on the
+ *     host in FP64 (libm exp, round to nearest even).
+ *   - Blume-Capel proposal: bit b = u & 1 picks the new value as the (b+1)-th
+ *     smallest of the two values different from the current one.
+ *   - Valid L: a multiple of 64 (each colour row is a whole number of 32-bit
+ *     words), 64 <= L <= 2^20 (Ising) or 2^19 (Blume-Capel), limited in
+ *     practice by free device memory.  Sweep indices must stay below 2^32.
+ *   - Every call returns an isg_status (0 = success) except the few that
+ *     return a size, a double or a string; no C++ exception or abort crosses
+ *     the ABI.  isg_last_error() gives a message for the calling thread.
+ *   - Device work is queued on the stream given at creation and is
+ *     asynchronous unless the call says it synchronises.  Calls on one
+ *     object from several host threads at once are not supported.
+ *   - The library owns the device memory it allocates.  The caller owns every
+ *     host array it passes and any device buffer it lends (device_buf).
+ *   - Without a usable CUDA device, the calls that need one return
+ *     ISG_ERR_UNSUPPORTED; nothing falls back to the CPU.
+ */
+#ifndef ISG_H
+#define ISG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t isg_status;
+#define ISG_OK 0
+#define ISG_ERR_INVALID (-1)        /* bad argument; nothing was queued           */
+#define ISG_ERR_OOM (-2)            /* device (or pinned host) allocation failed  */
+#define ISG_ERR_CUDA (-3)           /* a CUDA runtime call failed                 */
+#define ISG_ERR_DEVICE_TIMEOUT (-4) /* a bounded device-side wait gave up         */
+#define ISG_ERR_BUSY (-5)           /* no room (record ring full, server full)    */
+#define ISG_ERR_UNSUPPORTED (-6)    /* no usable CUDA device                      */
+
+#define ISG_ISING 0
+#define ISG_BLUME_CAPEL 1
+
+typedef struct isg_lattice isg_lattice;
+
+/* Creation parameters of one lattice. */
+typedef struct {
+    int32_t model;           /* ISG_ISING or ISG_BLUME_CAPEL                      */
+    int64_t L;               /* side; see "Valid L" above                         */
+    uint64_t seed;           /* Philox key of this lattice                        */
+    double delta;            /* crystal field Delta of Eq. (1); ignored for Ising */
+    void *stream;            /* cudaStream_t for all work, NULL = default stream  */
+    void *device_buf;        /* optional caller-owned device memory for the spins */
+    size_t device_buf_bytes; /* its size; must be >= isg_lattice_bytes(model, L)  */
+    int64_t record_capacity; /* observable records kept on the device (>= 1)      */
+} isg_lattice_desc;
+
+/* Observables of one lattice after one sweep (Eqs. (2)-(3); Appendix B).
+ *   B = sum_x s_x (s_{x+e1} + s_{x+e2})   (bond sum; energy per spin is
+ *                                          e = (-B + Delta Q) / L^2)
+ *   M = sum_x s_x,  Q = sum_x s_x^2,
+ *   row_sums[y] = sum_x s(x, y),  col_sums[x] = sum_y s(x, y).
+ * row_sums / col_sums point to caller-owned HOST arrays of L int32 each (or
+ * NULL to skip them). */
+typedef struct {
+    int64_t sweep; /* number of sweeps done when the record was taken         */
+    int64_t B, M, Q;
+    int32_t *row_sums;
+    int32_t *col_sums;
+} isg_obs;
+
+/* A piecewise-constant bath: beta(t) = beta[i] for t_start[i] <= t <
+ * t_start[i+1] (the last piece runs to the end).  t_start[0] must be <= the
+ * first sweep index used and t_start must increase.  This is the paper's
+ * time-dependent bath of the pre-cooling protocol ("Thermal protocols";
+ * Table II: T1 until t_switch, then T2). */
+typedef struct {
+    int64_t n_pieces;
+    const int64_t *t_start;
+    const double *beta;
+} isg_schedule;
+
+/* Bytes of device memory the spins of an L x L lattice occupy: L^2/8 for
+ * Ising (1 bit per site), L^2/4 for Blume-Capel (2 bit-planes).  0 if the
+ * model or L is invalid. */
+size_t isg_lattice_bytes(int32_t model, int64_t L);
+
+/* Create a lattice on the current CUDA device.  Allocates the spin planes
+ * (unless desc->device_buf is given) and the record ring (record_capacity
+ * records of 32 + 8 L bytes).  The spins are undefined until an init or set
+ * call.  *out is NULL on failure. */
+isg_status isg_lattice_create(const isg_lattice_desc *desc, isg_lattice **out);
+
+/* Release everything the lattice owns (waits for its stream first).  NULL is
+ * accepted. */
+void isg_lattice_destroy(isg_lattice *lat);
+
+/* Hot start ("Thermal protocols": the direct quench starts from T = infinity,
+ * a fully disordered configuration): Ising s = +1 iff u >= 2^31,
+ * Blume-Capel s = ((3 u) >> 32) - 1, u the site's hot-start random word.
+ * Resets the sweep counter to 0 and drops pending records. */
+isg_status isg_lattice_init_random(isg_lattice *lat);
+
+/* Cold start: every site = value (+1/-1; also 0 for Blume-Capel).  Resets
+ * the sweep counter to 0 and drops pending records. */
+isg_status isg_lattice_init_uniform(isg_lattice *lat, int8_t value);
+
+/* Load L*L host bytes (row-major, s[y*L + x]) and set the sweep counter to
+ * t.  Synchronises.  ISG_ERR_INVALID on a value outside the model's set. */
+isg_status isg_lattice_set(isg_lattice *lat, const int8_t *host, int64_t t);
+
+/* Copy the h x w window with corner (y0, x0), periodic wrap, to host bytes
+ * out[i*w + j] = s(x0 + j, y0 + i).  Synchronises. */
+isg_status isg_lattice_get_rect(isg_lattice *lat, int64_t y0, int64_t x0, int64_t h,
+                                int64_t w, int8_t *out);
+
+/* Whole lattice (L*L host bytes); the same as the rect with the full size. */
+isg_status isg_lattice_get(isg_lattice *lat, int8_t *out);
+
+/* Sweep counter (sweeps done so far), L, model, seed. */
+isg_status isg_lattice_info(const isg_lattice *lat, int64_t *sweep, int64_t *L,
+                            int32_t *model, uint64_t *seed);
+
+/* Run n Metropolis sweeps t0 .. t0+n-1 (t0 = the sweep counter), sweep t0+i
+ * at inverse temperature betas[i] (betas: n host doubles) or beta_const when
+ * betas is NULL.  beta must be >= 0 (+inf allowed: only dE <= 0 moves).
+ * With record_every = k > 0, the observables after every k-th sweep of this
+ * call are appended to the record ring; ISG_ERR_BUSY (nothing queued) if the
+ * ring has too little room.  Asynchronous. */
+isg_status isg_sweep(isg_lattice *lat, int64_t n, const double *betas, double beta_const,
+                     int64_t record_every);
+
+/* The same with beta(t) from a piecewise-constant schedule. */
+isg_status isg_sweep_schedule(isg_lattice *lat, int64_t n, const isg_schedule *sched,
+                              int64_t record_every);
+
+/* One half of the current sweep: colour 0 or 1 at inverse temperature beta.
+ * Colour 1 completes the sweep and advances the counter.  For timing a
+ * single kernel; isg_sweep is the normal entry. */
+isg_status isg_half_sweep(isg_lattice *lat, int32_t colour, double beta);
+
+/* Append the observables of the current lattice to the record ring.
+ * Asynchronous.  ISG_ERR_BUSY if the ring is full. */
+isg_status isg_record(isg_lattice *lat);
+
+/* Move up to max pending records, oldest first, into out[0..]: the scalars,
+ * and the row/column sums into the host arrays each out[i] points to (if not
+ * NULL).  *count = records moved.  Synchronises. */
+isg_status isg_read_records(isg_lattice *lat, isg_obs *out, int64_t max, int64_t *count);
+
+/* Number of records waiting in the ring. */
+isg_status isg_pending_records(const isg_lattice *lat, int64_t *count);
+
+/* Observables of the current lattice into *out (host arrays).  Does not touch
+ * the record ring.  Synchronises. */
+isg_status isg_measure(isg_lattice *lat, isg_obs *out);
+
+/* Second-moment correlation length of Appendix B for an ensemble of n
+ * lattices of side L, from their M[r] and row/column sums R[r*L + y],
+ * C[r*L + x] (host arrays):
+ *   S0 = M^2 (exact), Sk = (|M(2pi/L,0)|^2 + |M(0,2pi/L)|^2) / 2,
+ *   xi2 = sqrt(<S0>/<Sk> - 1) / (2 sin(pi/L)),
+ * replica averages taken first.  Host FP64 in a fixed operation order
+ * (twiddles from libm on the first octant and exact symmetries, compensated
+ * sums in index order), so equal integers give equal bits.  NaN if
+ * <S0> <= <Sk> or an argument is invalid; +inf if <Sk> = 0 < <S0>. */
+double isg_xi2(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const int32_t *C);
+
+/* Energy per spin (-B + Delta Q) / L^2 of one record. */
+double isg_energy_density(const isg_obs *obs, int64_t L, double delta);
+
+/* Human-readable message about the last failure in the calling thread. */
+const char *isg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ISG_H */

@@ -1,0 +1,74 @@
+"""Build libisg.so in-tree: nvcc for the sm_103a kernels and the C ABI, g++
+(-ffp-contract=off) for the host FP64 arithmetic, linked with the static
+CUDA runtime so that the library needs only the driver at run time.
+
+    python -m paper_2503_14688_b300.build        # or __graft_entry__.build()
+"""
+import os
+import shutil
+import subprocess
+import sys
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(PKG)
+CSRC = os.path.join(PKG, "csrc")
+INCLUDE = os.path.join(ROOT, "include")
+BUILD = os.path.join(PKG, "_build")
+LIB = os.path.join(PKG, "libisg.so")
+
+CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
+NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+CU_SOURCES = ["isg_kernels.cu", "isg_api.cu"]
+CPP_SOURCES = ["isg_host.cpp"]
+
+
+def _sources():
+    out = [os.path.join(CSRC, f) for f in CU_SOURCES + CPP_SOURCES]
+    out += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    out.append(os.path.join(INCLUDE, "isg.h"))
+    return out
+
+
+def _stale():
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(s) > t for s in _sources())
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    if not force and not _stale():
+        return LIB
+    os.makedirs(BUILD, exist_ok=True)
+    objs = []
+    inc = ["-I", INCLUDE, "-I", CSRC]
+    for f in CU_SOURCES:
+        obj = os.path.join(BUILD, f + ".o")
+        cmd = [NVCC, "-c", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+               "-Xcompiler", "-ffp-contract=off", *inc, os.path.join(CSRC, f), "-o", obj]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+        subprocess.run(cmd, check=True)
+        objs.append(obj)
+    for f in CPP_SOURCES:
+        obj = os.path.join(BUILD, f + ".o")
+        cmd = ["g++", "-c", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", "-Wall",
+               *inc, "-I", os.path.join(CUDA_HOME, "include"), os.path.join(CSRC, f), "-o", obj]
+        subprocess.run(cmd, check=True)
+        objs.append(obj)
+    tmp = LIB + ".tmp.%d" % os.getpid()
+    subprocess.run([NVCC, "-shared", *ARCH, "-o", tmp, *objs], check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+def clean():
+    shutil.rmtree(BUILD, ignore_errors=True)
+    if os.path.exists(LIB):
+        os.remove(LIB)
+
+
+if __name__ == "__main__":
+    print(build(force=True, verbose="-v" in sys.argv))

@@ -1,0 +1,81 @@
+// isg_internal.h -- types shared by the host side of libisg and its kernels.
+// Not part of the public ABI (that is include/isg.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace isg {
+
+// Philox4x32-10 multipliers and Weyl key increments (Salmon et al., SC'11).
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+// Launch-uniform part of the per-site Philox evaluation.  For a launch the
+// counter words 2 and 3 (sweep index, colour tag) and the key are fixed, so
+// half of the first round and a quarter of the second are the same for every
+// site; the host folds them here once per launch.
+struct PhiloxLaunch {
+    uint32_t rk0[10];  // round keys, word 0: key0 + r * W0
+    uint32_t rk1[10];  // round keys, word 1: key1 + r * W1
+    uint32_t r0_c0;    // round 0: hi(M1 * w2) ^ rk0[0]   (xor hi32(j>>2) per word)
+    uint32_t r0_c2x;   // round 0: w3 ^ rk1[0]            (xor hi(M0 * lo32(j>>2)))
+    uint32_t r1_c0x;   // round 1: lo(M1 * w2) ^ rk0[1]   (xor hi(M1 * c2'))
+};
+
+// Ising acceptance: a site with c anti-aligned neighbours has dE = 8 - 4c;
+// c >= 2 always flips, c = 1 flips iff u < thr4, c = 0 iff u < thr8.  A
+// threshold equal to 2^32 (always accept) is carried as full = ~0u.
+struct IsingThr {
+    uint32_t thr4, thr8;
+    uint32_t full4, full8;
+};
+
+// Blume-Capel acceptance table: entry (n << 6) | (p << 5) | (b << 4) | g
+// for the current value s (n = s != 0, p = s > 0), the proposal bit b and
+// g = h + 4 in [0, 8] (h = neighbour sum).  Accept iff (u >> 1) < entry;
+// entry = 2^31 means always.
+constexpr int kBcTableSize = 128;
+struct BcTable {
+    uint32_t thr[kBcTableSize];
+};
+
+// Device-side description of one lattice's spin planes.
+//   Ising:        plane(c)    = base + c * L * W          (bit = s > 0)
+//   Blume-Capel:  plane(c, 0) = base + (2c) * L * W       (n: s != 0)
+//                 plane(c, 1) = base + (2c + 1) * L * W   (p: s > 0, 0 if s = 0)
+// W = L / 64 words per row; bit b of word w of row y is the site with
+// same-colour row index i = 32 w + b, x = 2 i + ((c ^ y) & 1).
+struct Planes {
+    uint32_t *base;
+    int64_t L;
+    int64_t W;
+    int32_t model;
+};
+
+// Record layout in device memory: int64 [sweep, B, M, Q] then int32 R[L],
+// int32 C[L].
+inline size_t record_stride(int64_t L) { return 32 + 8 * (size_t)L; }
+
+// ---- host helpers (isg_host.cpp) ----
+void philox_launch_consts(uint64_t seed, uint32_t w2, uint32_t w3, PhiloxLaunch *out);
+void ising_thresholds(double beta, IsingThr *out);
+void bc_table(double beta, double delta, BcTable *out);
+double xi2_fp64(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const int32_t *C);
+
+// ---- kernel launchers (isg_kernels.cu); return the launch error ----
+cudaError_t launch_init_random(const Planes &pl, const PhiloxLaunch &ph0, const PhiloxLaunch &ph1,
+                               cudaStream_t st);
+cudaError_t launch_init_uniform(const Planes &pl, int value, cudaStream_t st);
+cudaError_t launch_half_sweep(const Planes &pl, int colour, const PhiloxLaunch &ph,
+                              const IsingThr &ithr, const BcTable *btab, cudaStream_t st);
+cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaStream_t st);
+cudaError_t launch_pack(const Planes &pl, const int8_t *d_spins, int32_t *d_bad, cudaStream_t st);
+cudaError_t launch_unpack_rect(const Planes &pl, int64_t y0, int64_t x0, int64_t h, int64_t w,
+                               int8_t *d_out, cudaStream_t st);
+
+}  // namespace isg
