@@ -15,6 +15,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libisg.so")
+CALIB_LIB = os.path.join(PKG, "libisg_calib.so")
 
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
@@ -32,10 +33,11 @@ def _sources():
 
 
 def _stale():
-    if not os.path.exists(LIB):
-        return True
-    t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(s) > t for s in _sources())
+    for lib in (LIB, CALIB_LIB):
+        if not os.path.exists(lib):
+            return True
+    t = min(os.path.getmtime(LIB), os.path.getmtime(CALIB_LIB))
+    return any(os.path.getmtime(s) > t for s in _sources() + [os.path.join(CSRC, "isg_calib.cu")])
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -61,13 +63,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + ".tmp.%d" % os.getpid()
     subprocess.run([NVCC, "-shared", *ARCH, "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
+    # integer-throughput calibration kernels (roofline measurement tool)
+    tmp = CALIB_LIB + ".tmp.%d" % os.getpid()
+    subprocess.run([NVCC, "-shared", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
+                    os.path.join(CSRC, "isg_calib.cu"), "-o", tmp], check=True)
+    os.replace(tmp, CALIB_LIB)
     return LIB
 
 
 def clean():
     shutil.rmtree(BUILD, ignore_errors=True)
-    if os.path.exists(LIB):
-        os.remove(LIB)
+    for lib in (LIB, CALIB_LIB):
+        if os.path.exists(lib):
+            os.remove(lib)
 
 
 if __name__ == "__main__":
