@@ -177,6 +177,38 @@ isg_status isg_pending_records(const isg_lattice *lat, int64_t *count);
  * the record ring.  Synchronises. */
 isg_status isg_measure(isg_lattice *lat, isg_obs *out);
 
+/* Largest L accepted by isg_measure_planes_noalloc. */
+#define ISG_NOALLOC_MAX_L ((int64_t)1 << 18)
+
+/* The paper has no counterpart of this call: it serves callers that cannot
+ * allocate device memory when they measure -- a process whose device memory
+ * is all handed out by its own pool allocator, or a loop running many
+ * lattices on concurrent streams that cannot afford the device-wide
+ * synchronisation cudaMalloc/cudaFree may cause.
+ *
+ * Same observables as isg_measure (B, M, Q and, if the out pointers are not
+ * NULL, the row/column sums into caller HOST arrays of L int32 each), for
+ * spin planes held in caller memory: d_planes is a device pointer to
+ * isg_lattice_bytes(model, L) bytes in the plane layout that a lattice
+ * created with that buffer as device_buf keeps there (16-byte aligned, read
+ * only).  out->sweep is set to `sweep` (a label of the caller's choosing).
+ * Work is queued on `stream` (NULL = default stream) and the call waits for
+ * that stream before returning.
+ *
+ * Allocates nothing: it accumulates into one fixed array of 32 + 8 L bytes
+ * for L <= ISG_NOALLOC_MAX_L (2 MiB + 32 bytes) in the library's device
+ * image, which every GPU that loads the library holds until the process
+ * exits.  L above that limit is rejected with ISG_ERR_INVALID (use
+ * isg_measure).  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Each call clears the part of the array it
+ * uses before accumulating.  All calls on one device share the array: calls
+ * whose GPU work overlaps (for instance from two host threads on two
+ * streams) race on it and their results are undefined; calls made one after
+ * another never overlap, since each waits for its stream. */
+isg_status isg_measure_planes_noalloc(int32_t model, int64_t L, const void *d_planes,
+                                      void *stream, int64_t sweep, isg_obs *out);
+
 /* Second-moment correlation length of Appendix B for an ensemble of n
  * lattices of side L, from their M[r] and row/column sums R[r*L + y],
  * C[r*L + x] (host arrays):

@@ -17,6 +17,7 @@ ISG_ERR_CUDA = -3
 ISG_ERR_DEVICE_TIMEOUT = -4
 ISG_ERR_BUSY = -5
 ISG_ERR_UNSUPPORTED = -6
+ISG_NOALLOC_MAX_L = 1 << 18
 ISG_ISING = 0
 ISG_BLUME_CAPEL = 1
 
@@ -68,6 +69,7 @@ PROTOTYPES = {
     "isg_read_records": (_I32, [_P, ctypes.POINTER(isg_obs), _I64, _I64P]),
     "isg_pending_records": (_I32, [_P, _I64P]),
     "isg_measure": (_I32, [_P, ctypes.POINTER(isg_obs)]),
+    "isg_measure_planes_noalloc": (_I32, [_I32, _I64, _P, _P, _I64, ctypes.POINTER(isg_obs)]),
     "isg_xi2": (_F64, [_I64, _I64, _I64P, _I32P, _I32P]),
     "isg_energy_density": (_F64, [ctypes.POINTER(isg_obs), _I64, _F64]),
     "isg_last_error": (ctypes.c_char_p, []),

@@ -56,6 +56,19 @@ bool valid_beta(double b) { return !std::isnan(b) && b >= 0.0; }
 
 }  // namespace
 
+namespace isg {
+
+int32_t report_error(int32_t code, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+}  // namespace isg
+
 struct isg_lattice {
     int32_t model;
     int64_t L, W;

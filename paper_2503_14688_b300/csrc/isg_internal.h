@@ -67,6 +67,10 @@ void ising_thresholds(double beta, IsingThr *out);
 void bc_table(double beta, double delta, BcTable *out);
 double xi2_fp64(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const int32_t *C);
 
+// ---- error reporting shared by the C-ABI files (isg_api.cu) ----
+// Stores a printf-style message for isg_last_error() and returns code.
+int32_t report_error(int32_t code, const char *fmt, ...);
+
 // ---- kernel launchers (isg_kernels.cu); return the launch error ----
 cudaError_t launch_init_random(const Planes &pl, const PhiloxLaunch &ph0, const PhiloxLaunch &ph1,
                                cudaStream_t st);

@@ -176,3 +176,18 @@ def xi2(M, R, C) -> float:
     L = R.size // max(n, 1)
     return float(lib().isg_xi2(n, L, M.ctypes.data_as(_abi._I64P), R.ctypes.data_as(_abi._I32P),
                                C.ctypes.data_as(_abi._I32P)))
+
+
+def measure_planes_noalloc(model: int, L: int, planes, stream=None, sweep: int = 0) -> Obs:
+    """isg_measure_planes_noalloc: observables of spin planes held in caller
+    device memory (``planes``: a torch tensor or a raw device address), with
+    no device allocation inside the call."""
+    ptr = planes if isinstance(planes, int) else int(planes.data_ptr())
+    R = np.zeros(L, dtype=np.int32)
+    C = np.zeros(L, dtype=np.int32)
+    o = _abi.isg_obs()
+    o.row_sums = R.ctypes.data_as(_abi._I32P)
+    o.col_sums = C.ctypes.data_as(_abi._I32P)
+    check(lib().isg_measure_planes_noalloc(int(model), int(L), ptr, _stream_handle(stream),
+                                           int(sweep), ctypes.byref(o)))
+    return Obs(o.sweep, o.B, o.M, o.Q, R, C)
