@@ -17,6 +17,8 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*``):
                   beta = infinity limits, global spin-flip symmetry
   measure         pinned: invariants and closed forms on constructed lattices
   xi2             pinned: closed forms on constructed row/column sums
+  window_init/run pinned: equal to init_random/run on the interior of the
+                  light cone (tests/test_oracle_windows.py)
 """
 import ctypes
 import os
@@ -61,6 +63,13 @@ def lib():
         L.oracle_run.restype = ctypes.c_int64
         L.oracle_xi2.argtypes = [ctypes.c_int64, ctypes.c_int64, i64p, i32p, i32p]
         L.oracle_xi2.restype = ctypes.c_double
+        L.oracle_window_init.argtypes = [i8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64]
+        L.oracle_window_init.restype = ctypes.c_int
+        L.oracle_window_run.argtypes = [i8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                        ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
+                                        ctypes.c_uint64, ctypes.c_int64, f64p, ctypes.c_double]
+        L.oracle_window_run.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -159,3 +168,27 @@ def xi2(M, R, C) -> float:
     assert R.size == n * L and C.size == n * L
     return float(lib().oracle_xi2(n, L, _ptr(M, ctypes.c_int64), _ptr(R, ctypes.c_int32),
                                   _ptr(C, ctypes.c_int32)))
+
+
+def window_init(h: int, w: int, y0: int, x0: int, L: int, model: int, seed: int) -> np.ndarray:
+    """Hot start of the h x w window at (y0, x0) of an L x L lattice (global keys)."""
+    s = np.zeros((h, w), dtype=np.int8)
+    rc = lib().oracle_window_init(_ptr(s, ctypes.c_int8), h, w, y0, x0, L, model,
+                                  seed & (2**64 - 1))
+    if rc != 0:
+        raise ValueError("oracle_window_init rejected its arguments")
+    return s
+
+
+def window_run(s: np.ndarray, y0: int, x0: int, L: int, model: int, seed: int, t0: int, betas,
+               delta: float = 0.0):
+    """Sweep a window in place with global keys, its outer ring held fixed;
+    after n sweeps the sites farther than 2n from the ring are exact."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    h, w = s.shape
+    betas = np.ascontiguousarray(np.asarray(betas, dtype=np.float64).reshape(-1))
+    rc = lib().oracle_window_run(_ptr(s, ctypes.c_int8), h, w, y0, x0, L, model,
+                                 seed & (2**64 - 1), t0, betas.size,
+                                 _ptr(betas, ctypes.c_double), float(delta))
+    if rc != 0:
+        raise ValueError("oracle_window_run rejected its arguments")

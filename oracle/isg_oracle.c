@@ -416,3 +416,80 @@ double oracle_xi2(int64_t n, int64_t L, const int64_t *M, const int32_t *R, cons
         return INFINITY;
     return sqrt(s0avg / skavg - 1.0) / (2.0 * sin(M_PI / (double)L));
 }
+
+/* ------------------------------------------------------------------------ */
+/* Windows of a large lattice (light-cone checks).                           */
+/* ------------------------------------------------------------------------ */
+
+/* Hot start of the h x w window with corner (y0, x0) of the L x L lattice:
+ * s[i*w + j] is site ((x0 + j) mod L, (y0 + i) mod L), drawn exactly as
+ * oracle_init_random draws it (global colour and same-colour index).       */
+int oracle_window_init(int8_t *s, int64_t h, int64_t w, int64_t y0, int64_t x0, int64_t L,
+                       int model, uint64_t seed)
+{
+    if (!s || h < 1 || w < 1 || L < 2 || (model != ORACLE_ISING && model != ORACLE_BLUME_CAPEL))
+        return -1;
+    for (int64_t i = 0; i < h; ++i) {
+        const int64_t y = (y0 + i) % L;
+        for (int64_t j = 0; j < w; ++j) {
+            const int64_t x = (x0 + j) % L;
+            const uint64_t idx = (uint64_t)(y * L + x);
+            const uint32_t c = (uint32_t)((x + y) & 1);
+            const uint32_t u = site_word(seed, idx >> 1, 0u, c | 2u);
+            if (model == ORACLE_ISING)
+                s[i * w + j] = (int8_t)(u >= 0x80000000u ? 1 : -1);
+            else
+                s[i * w + j] = (int8_t)((int)(((uint64_t)u * 3u) >> 32) - 1);
+        }
+    }
+    return 0;
+}
+
+/* n sweeps t0 .. t0+n-1 of the window: every site except the outer ring is
+ * updated with the random word and colour of its global position; the ring
+ * is held fixed (it stands for the unknown rest of the lattice).  After n
+ * sweeps the sites at distance > 2n from the ring are exactly those of the
+ * full lattice (each half-sweep lets an error move one site).  L even.     */
+int oracle_window_run(int8_t *s, int64_t h, int64_t w, int64_t y0, int64_t x0, int64_t L,
+                      int model, uint64_t seed, uint64_t t0, int64_t n, const double *betas,
+                      double delta)
+{
+    if (!s || h < 3 || w < 3 || L < 2 || L % 2 != 0 || n < 0 || !betas ||
+        (model != ORACLE_ISING && model != ORACLE_BLUME_CAPEL))
+        return -1;
+    for (int64_t k = 0; k < n; ++k) {
+        const uint64_t t = t0 + (uint64_t)k;
+        for (int c = 0; c < 2; ++c) {
+            for (int64_t i = 1; i < h - 1; ++i) {
+                const int64_t y = (y0 + i) % L;
+                for (int64_t j = 1; j < w - 1; ++j) {
+                    const int64_t x = (x0 + j) % L;
+                    if ((int)((x + y) & 1) != c)
+                        continue;
+                    const uint64_t jj = (uint64_t)(y * L + x) >> 1;
+                    const uint32_t u = site_word(seed, jj, (uint32_t)t, (uint32_t)c);
+                    const int64_t id = i * w + j;
+                    const int si = s[id];
+                    const int hsum = s[id - 1] + s[id + 1] + s[id - w] + s[id + w];
+                    if (model == ORACLE_ISING) {
+                        const double dE = (double)(2 * si * hsum);
+                        int accept = 1;
+                        if (dE > 0.0)
+                            accept = (uint64_t)u < threshold_bits(betas[k], dE, 32);
+                        if (accept)
+                            s[id] = (int8_t)(-si);
+                    } else {
+                        const int s2 = oracle_bc_proposal(si, (int)(u & 1u));
+                        const double dE = bc_delta_energy(si, s2, hsum, delta);
+                        int accept = 1;
+                        if (dE > 0.0)
+                            accept = (uint64_t)(u >> 1) < threshold_bits(betas[k], dE, 31);
+                        if (accept)
+                            s[id] = (int8_t)s2;
+                    }
+                }
+            }
+        }
+    }
+    return 0;
+}
