@@ -30,6 +30,7 @@ namespace isg {
 namespace {
 
 constexpr int kSweepThreads = 128;
+constexpr int kSweepMinBlocks = 12;  // 40 registers: 48 warps per SM
 constexpr int kMeasureThreads = 256;
 
 template <int V>
@@ -182,8 +183,19 @@ __global__ void k_init_uniform(Planes pl, int value)
 // up/same/down neighbour words in registers (each neighbour word is loaded
 // once per band plus two halo rows).
 // ---------------------------------------------------------------------------
+// acc * 2 + (u >= thr): the compare is the borrow of u - thr, shifted into the
+// accumulator by an add-with-carry -- two integer instructions per compare.
+__device__ __forceinline__ uint32_t shift_in_not_below(uint32_t acc, uint32_t u, uint32_t thr)
+{
+    uint32_t out;
+    asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}"
+        : "=r"(out)
+        : "r"(u), "r"(thr), "r"(acc));
+    return out;
+}
+
 template <int V>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
     k_ising_half(uint32_t *__restrict__ tgt, const uint32_t *__restrict__ nbr, int64_t L,
                  int64_t W, int colour, int H, PhiloxLaunch pc, IsingThr thr)
 {
@@ -207,19 +219,23 @@ __global__ void __launch_bounds__(kSweepThreads)
         for (int v = 0; v < V; ++v) {
             const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)(w0 + v);
             const PhiloxWordPart wp = philox_word_part(pc, (uint32_t)(q0 >> 32));
-            uint32_t a4 = 0, a8 = 0;
+            // reject masks: bit 4i+k set iff site 4i+k's word >= the threshold
+            uint32_t r4 = 0, r8 = 0;
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
                 uint32_t r[4];
                 philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
+                uint32_t n4 = 0, n8 = 0;
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    a4 |= (uint32_t)(r[k] < thr.thr4) << (4 * i + k);
-                    a8 |= (uint32_t)(r[k] < thr.thr8) << (4 * i + k);
+                for (int k = 3; k >= 0; --k) {
+                    n4 = shift_in_not_below(n4, r[k], thr.thr4);
+                    n8 = shift_in_not_below(n8, r[k], thr.thr8);
                 }
+                r4 = n4 * (1u << (4 * i)) + r4;
+                r8 = n8 * (1u << (4 * i)) + r8;
             }
-            a4 |= thr.full4;
-            a8 |= thr.full8;
+            const uint32_t a4 = ~r4 | thr.full4;
+            const uint32_t a8 = ~r8 | thr.full8;
             const uint32_t t = T.v[v];
             // anti-aligned neighbour indicators and their bit-sliced count
             const uint32_t a = t ^ U.v[v], b = t ^ D.v[v], d = t ^ S.v[v], e = t ^ X.v[v];
@@ -340,89 +356,115 @@ __global__ void __launch_bounds__(kSweepThreads)
 
 // ---------------------------------------------------------------------------
 // Observables.  A thread owns one word column w of both colours over a band
-// of H rows.  Bonds: every bond joins a colour-0 and a colour-1 site, so
-// B = sum over colour-1 sites of s * (sum of its four colour-0 neighbours).
-// Row sums: a warp's lanes share the row, reduced by shuffles into a
-// shared-memory array for the band, then one global atomic per row and block.
-// Column sums: per bit position, vertical bit-sliced counters of the +1 (and
-// for Blume-Capel the -1) sites, split by column parity; at the end of the
-// band they are read out per column and added atomically.
+// of H rows (a multiple of 16), walked in groups of four rows whose loads are
+// issued together.  Bonds: every bond joins a colour-0 and a colour-1 site,
+// so B = sum over colour-1 sites of s * (sum of its four colour-0
+// neighbours).  Row sums: the 32 lanes of a warp share the row; one warp
+// reduction per row into a shared-memory array for the band, then one global
+// atomic per row and block.  Column sums: per bit position, carry-save
+// (Harley-Seal) counters of the +1 (and for Blume-Capel the -1) sites, split
+// by column parity; every 16 rows the carry of weight 16 ripples into a
+// bit-sliced high counter.  At the end of the band each column's count is
+// read out and added atomically.
 // ---------------------------------------------------------------------------
-constexpr int kCountBits = 13;  // band height < 2^13
-constexpr int kMeasureBand = 4096;
+constexpr int kMeasureBand = 8192;  // rows per band at most
+constexpr int kHighBits = 10;       // high counter: multiples of 16 up to 16 * 1023
 
-__device__ __forceinline__ void vcount_add(uint32_t (&c)[kCountBits], uint32_t x)
+struct ColumnCounter {
+    uint32_t ones, twos, fours, eights;
+    uint32_t high[kHighBits];
+    uint32_t fa, ea;  // pending carries of weight 4 and 8 inside a 16-row block
+};
+
+__device__ __forceinline__ void csa(uint32_t &acc, uint32_t b, uint32_t c, uint32_t &carry)
 {
+    const uint32_t u = acc ^ b;
+    carry = (acc & b) | (u & c);
+    acc = u ^ c;
+}
+
+// Add the four words of one 4-row group; g = group index within the 16-row
+// block (0..3).
+__device__ __forceinline__ void cc_add4(ColumnCounter &k, uint32_t w0, uint32_t w1, uint32_t w2,
+                                        uint32_t w3, int g)
+{
+    uint32_t ta, tb, f;
+    csa(k.ones, w0, w1, ta);
+    csa(k.ones, w2, w3, tb);
+    csa(k.twos, ta, tb, f);
+    if ((g & 1) == 0) {
+        k.fa = f;
+        return;
+    }
+    uint32_t e;
+    csa(k.fours, k.fa, f, e);
+    if (g == 1) {
+        k.ea = e;
+        return;
+    }
+    uint32_t sixteen;
+    csa(k.eights, k.ea, e, sixteen);
 #pragma unroll
-    for (int l = 0; l < kCountBits; ++l) {
-        const uint32_t carry = c[l] & x;
-        c[l] ^= x;
-        x = carry;
-        if (x == 0)
-            break;
+    for (int l = 0; l < kHighBits; ++l) {
+        const uint32_t c = k.high[l] & sixteen;
+        k.high[l] ^= sixteen;
+        sixteen = c;
     }
 }
 
-__device__ __forceinline__ int vcount_get(const uint32_t (&c)[kCountBits], int bit)
+__device__ __forceinline__ int cc_get(const ColumnCounter &k, int bit)
 {
-    int v = 0;
+    int v = (int)((k.ones >> bit) & 1u) + 2 * (int)((k.twos >> bit) & 1u) +
+            4 * (int)((k.fours >> bit) & 1u) + 8 * (int)((k.eights >> bit) & 1u);
+    int h = 0;
 #pragma unroll
-    for (int l = 0; l < kCountBits; ++l)
-        v |= (int)((c[l] >> bit) & 1u) << l;
-    return v;
+    for (int l = 0; l < kHighBits; ++l)
+        h |= (int)((k.high[l] >> bit) & 1u) << l;
+    return v + 16 * h;
 }
 
-__device__ __forceinline__ int64_t warp_sum64(int64_t v)
+__device__ __forceinline__ void cc_zero(ColumnCounter &k)
 {
+    k.ones = k.twos = k.fours = k.eights = k.fa = k.ea = 0;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
-}
-
-__device__ __forceinline__ int warp_sum32(int v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-        v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
+    for (int l = 0; l < kHighBits; ++l)
+        k.high[l] = 0;
 }
 
 template <int MODEL>
-__global__ void __launch_bounds__(kMeasureThreads)
+__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
     k_measure(Planes pl, int H, int64_t *__restrict__ rec_hdr, int32_t *__restrict__ R,
               int32_t *__restrict__ C, int64_t sweep)
 {
     __shared__ int32_t s_row[kMeasureBand];
     const int64_t L = pl.L, W = pl.W, LW = L * W;
     const int64_t y0 = (int64_t)blockIdx.y * H;
-    const int64_t y1 = y0 + H < L ? y0 + H : L;
-    for (int i = threadIdx.x; i < H; i += blockDim.x)
+    const int rows = (int)((y0 + H < L ? y0 + H : L) - y0);  // a multiple of 16
+    for (int i = threadIdx.x; i < rows; i += blockDim.x)
         s_row[i] = 0;
     __syncthreads();
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0)
         rec_hdr[0] = sweep;
 
     const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const bool active = w < W && y0 < L;
+    const bool active = w < W;
     const int64_t wc = active ? w : 0;
-    // plane pointers: colour c, bit-plane k
-    const uint32_t *n0 = pl.base, *n1, *p0, *p1;
-    if (MODEL == 0) {
-        p0 = pl.base;
-        p1 = pl.base + LW;
-        n0 = n1 = nullptr;
-    } else {
-        n0 = pl.base;
-        p0 = pl.base + LW;
-        n1 = pl.base + 2 * LW;
-        p1 = pl.base + 3 * LW;
+    // plane pointers: colour-0 / colour-1 sign planes (and occupancy planes)
+    const uint32_t *p0 = MODEL == 0 ? pl.base : pl.base + LW;
+    const uint32_t *p1 = MODEL == 0 ? pl.base + LW : pl.base + 3 * LW;
+    const uint32_t *n0 = pl.base, *n1 = pl.base + 2 * LW;  // Blume-Capel only
+    const int64_t wl = wc == 0 ? W - 1 : wc - 1, wr = wc + 1 == W ? 0 : wc + 1;
+
+    int accB = 0, accM = 0, accQ = 0;
+    ColumnCounter ce_p, co_p, ce_m, co_m;  // even/odd columns, +1 / -1 sites
+    cc_zero(ce_p);
+    cc_zero(co_p);
+    if (MODEL == 1) {
+        cc_zero(ce_m);
+        cc_zero(co_m);
     }
-    int64_t accB = 0, accM = 0, accQ = 0;
-    uint32_t ce_p[kCountBits] = {}, co_p[kCountBits] = {};
-    uint32_t ce_m[kCountBits] = {}, co_m[kCountBits] = {};
     const int64_t yup = y0 == 0 ? L - 1 : y0 - 1;
-    uint32_t Up = 0, Sp = 0, Un = ~0u, Sn = ~0u;
+    uint32_t Up = 0, Sp = 0, Un = 0, Sn = 0;
     if (active) {
         Up = __ldg(p0 + yup * W + wc);
         Sp = __ldg(p0 + y0 * W + wc);
@@ -431,83 +473,107 @@ __global__ void __launch_bounds__(kMeasureThreads)
             Sn = __ldg(n0 + y0 * W + wc);
         }
     }
-    for (int64_t y = y0; y < y1; ++y) {
-        int rowpart = 0;
-        if (active) {
-            const int64_t yd = y + 1 == L ? 0 : y + 1;
-            const int par1 = (1 ^ (int)y) & 1;  // colour-1 parity of row y
-            const int64_t ew = y * W + edge_word(wc, 1, W, par1);
-            const uint32_t Dp = __ldg(p0 + yd * W + wc);
-            const uint32_t Xp = par1 == 0 ? (Sp << 1) | (__ldg(p0 + ew) >> 31)
-                                          : (Sp >> 1) | (__ldg(p0 + ew) << 31);
-            const uint32_t Tp = __ldg(p1 + y * W + wc);
-            if (MODEL == 0) {
-                const int anti = __popc(Tp ^ Up) + __popc(Tp ^ Dp) + __popc(Tp ^ Sp) +
-                                 __popc(Tp ^ Xp);
-                accB += 128 - 2 * anti;
-                const int ones = __popc(Tp) + __popc(Sp);
-                rowpart = 2 * ones - 64;
-                const uint32_t E = (y & 1) ? Tp : Sp, O = (y & 1) ? Sp : Tp;
-                vcount_add(ce_p, E);
-                vcount_add(co_p, O);
-                Up = Sp;
-                Sp = Dp;
-            } else {
-                const uint32_t Dn = __ldg(n0 + yd * W + wc);
-                const uint32_t Xn = par1 == 0 ? (Sn << 1) | (__ldg(n0 + ew) >> 31)
-                                              : (Sn >> 1) | (__ldg(n0 + ew) << 31);
-                const uint32_t Tn = __ldg(n1 + y * W + wc);
-                const uint32_t nb[4] = {Un, Dn, Sn, Xn}, pb[4] = {Up, Dp, Sp, Xp};
+    for (int r0 = 0; r0 < rows; r0 += 16) {
+#pragma unroll 1
+        for (int g = 0; g < 4; ++g) {
+            const int64_t yg = y0 + r0 + 4 * g;
+            uint32_t Tp[4], Dp[4], Ep[4], Tn[4], Dn[4], En[4];
+            if (active) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t both = Tn & nb[k];
-                    accB += __popc(both) - 2 * __popc(both & (Tp ^ pb[k]));
+                for (int r = 0; r < 4; ++r) {
+                    const int64_t y = yg + r;
+                    const int64_t yd = y + 1 == L ? 0 : y + 1;
+                    // colour-1 parity (1 ^ y) & 1: 0 -> left neighbour word, 1 -> right
+                    const int64_t ew = y * W + ((y & 1) ? wl : wr);
+                    Tp[r] = __ldg(p1 + y * W + wc);
+                    Dp[r] = __ldg(p0 + yd * W + wc);
+                    Ep[r] = __ldg(p0 + ew);
+                    if (MODEL == 1) {
+                        Tn[r] = __ldg(n1 + y * W + wc);
+                        Dn[r] = __ldg(n0 + yd * W + wc);
+                        En[r] = __ldg(n0 + ew);
+                    }
                 }
-                const uint32_t plus1 = Tn & Tp, minus1 = Tn & ~Tp;
-                const uint32_t plus0 = Sn & Sp, minus0 = Sn & ~Sp;
-                rowpart = __popc(plus1) + __popc(plus0) - __popc(minus1) - __popc(minus0);
-                accQ += __popc(Tn) + __popc(Sn);
-                const bool odd = y & 1;
-                vcount_add(ce_p, odd ? plus1 : plus0);
-                vcount_add(co_p, odd ? plus0 : plus1);
-                vcount_add(ce_m, odd ? minus1 : minus0);
-                vcount_add(co_m, odd ? minus0 : minus1);
-                Un = Sn;
-                Sn = Dn;
-                Up = Sp;
-                Sp = Dp;
+            } else {
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    Tp[r] = Dp[r] = Ep[r] = Tn[r] = Dn[r] = En[r] = 0;
             }
-            accM += rowpart;
+            uint32_t evp[4], odp[4], evm[4], odm[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const bool odd = (yg + r) & 1;
+                const uint32_t Xp = odd ? (Sp << 1) | (Ep[r] >> 31) : (Sp >> 1) | (Ep[r] << 31);
+                int rowpart;
+                if (MODEL == 0) {
+                    const uint32_t T = Tp[r];
+                    const int anti = __popc(T ^ Up) + __popc(T ^ Dp[r]) + __popc(T ^ Sp) +
+                                     __popc(T ^ Xp);
+                    accB += 128 - 2 * anti;
+                    rowpart = 2 * (__popc(T) + __popc(Sp)) - 64;
+                    evp[r] = odd ? T : Sp;
+                    odp[r] = odd ? Sp : T;
+                } else {
+                    const uint32_t Xn = odd ? (Sn << 1) | (En[r] >> 31) : (Sn >> 1) | (En[r] << 31);
+                    const uint32_t Tn_ = Tn[r], Tp_ = Tp[r];
+                    const uint32_t nb[4] = {Un, Dn[r], Sn, Xn}, pb[4] = {Up, Dp[r], Sp, Xp};
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t both = Tn_ & nb[k];
+                        accB += __popc(both) - 2 * __popc(both & (Tp_ ^ pb[k]));
+                    }
+                    const uint32_t plus1 = Tn_ & Tp_, minus1 = Tn_ & ~Tp_;
+                    const uint32_t plus0 = Sn & Sp, minus0 = Sn & ~Sp;
+                    rowpart = __popc(plus1) + __popc(plus0) - __popc(minus1) - __popc(minus0);
+                    accQ += __popc(Tn_) + __popc(Sn);
+                    evp[r] = odd ? plus1 : plus0;
+                    odp[r] = odd ? plus0 : plus1;
+                    evm[r] = odd ? minus1 : minus0;
+                    odm[r] = odd ? minus0 : minus1;
+                    Un = Sn;
+                    Sn = Dn[r];
+                }
+                if (!active)
+                    rowpart = 0;
+                accM += rowpart;
+                const int rs = __reduce_add_sync(0xFFFFFFFFu, rowpart);
+                if ((threadIdx.x & 31) == 0)
+                    atomicAdd(&s_row[r0 + 4 * g + r], rs);
+                Up = Sp;
+                Sp = Dp[r];
+            }
+            cc_add4(ce_p, evp[0], evp[1], evp[2], evp[3], g);
+            cc_add4(co_p, odp[0], odp[1], odp[2], odp[3], g);
+            if (MODEL == 1) {
+                cc_add4(ce_m, evm[0], evm[1], evm[2], evm[3], g);
+                cc_add4(co_m, odm[0], odm[1], odm[2], odm[3], g);
+            }
         }
-        const int rs = warp_sum32(rowpart);
-        if ((threadIdx.x & 31) == 0 && y < y1)
-            atomicAdd(&s_row[y - y0], rs);
     }
+    if (!active)
+        accB = accQ = 0;
     if (MODEL == 0)
-        accQ = active ? 64 * (y1 - y0) : 0;
-    accB = warp_sum64(accB);
-    accM = warp_sum64(accM);
-    accQ = warp_sum64(accQ);
+        accQ = active ? 64 * rows : 0;
+    accB = __reduce_add_sync(0xFFFFFFFFu, accB);
+    accM = __reduce_add_sync(0xFFFFFFFFu, accM);
+    accQ = __reduce_add_sync(0xFFFFFFFFu, accQ);
     if ((threadIdx.x & 31) == 0) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 1), (unsigned long long)accB);
-        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 2), (unsigned long long)accM);
-        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 3), (unsigned long long)accQ);
+        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 1), (unsigned long long)(int64_t)accB);
+        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 2), (unsigned long long)(int64_t)accM);
+        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 3), (unsigned long long)(int64_t)accQ);
     }
     if (active) {
-        const int rows = (int)(y1 - y0);
-        // rows of each column parity in the band: even columns take colour 0
-        // on even rows and colour 1 on odd rows, so every column gets one
-        // site per row.
+        // every column gets one site per row of the band
 #pragma unroll 4
         for (int b = 0; b < 32; ++b) {
             const int64_t xe = 2 * (32 * wc + b);
             int ve, vo;
             if (MODEL == 0) {
-                ve = 2 * vcount_get(ce_p, b) - rows;
-                vo = 2 * vcount_get(co_p, b) - rows;
+                ve = 2 * cc_get(ce_p, b) - rows;
+                vo = 2 * cc_get(co_p, b) - rows;
             } else {
-                ve = vcount_get(ce_p, b) - vcount_get(ce_m, b);
-                vo = vcount_get(co_p, b) - vcount_get(co_m, b);
+                ve = cc_get(ce_p, b) - cc_get(ce_m, b);
+                vo = cc_get(co_p, b) - cc_get(co_m, b);
             }
             if (ve)
                 atomicAdd(&C[xe], ve);
@@ -516,7 +582,7 @@ __global__ void __launch_bounds__(kMeasureThreads)
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < (int)(y1 - y0); i += blockDim.x)
+    for (int i = threadIdx.x; i < rows; i += blockDim.x)
         if (s_row[i])
             atomicAdd(&R[y0 + i], s_row[i]);
 }
@@ -581,13 +647,18 @@ __global__ void k_unpack_rect(Planes pl, int64_t y0, int64_t x0, int64_t h, int6
     out[gid] = (int8_t)v;
 }
 
-// Rows per thread for a sweep launch: enough threads to fill the GPU a few
-// times over, at most 64 rows per band.
+// Rows per thread for a sweep launch: at most 64, fewer while the grid would
+// give less than about eight waves of resident blocks (tail balance), more
+// if the number of row bands would exceed the grid's y limit.
 int sweep_band(int64_t L, int64_t threads_per_row)
 {
+    const int64_t bx = (threads_per_row + kSweepThreads - 1) / kSweepThreads;
+    const int64_t want_blocks = 148LL * kSweepMinBlocks * 8;
     int H = 64;
-    while (H > 1 && (L / H) * threads_per_row < 148LL * 2048)
+    while (H > 1 && bx * (L / H) < want_blocks)
         H >>= 1;
+    while ((L + H - 1) / H > 65535)
+        H <<= 1;
     return H;
 }
 
@@ -663,13 +734,18 @@ cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaSt
     int64_t *hdr = reinterpret_cast<int64_t *>(record);
     int32_t *R = reinterpret_cast<int32_t *>(hdr + 4);
     int32_t *C = R + pl.L;
-    const int H = (int)(pl.L < kMeasureBand ? pl.L : kMeasureBand);
-    const dim3 grid((unsigned)((pl.W + kMeasureThreads - 1) / kMeasureThreads),
-                    (unsigned)((pl.L + H - 1) / H));
+    // band height: a multiple of 16 (L is a multiple of 64, so every band,
+    // the last included, has a multiple of 16 rows), as tall as possible
+    // (fewer column atomics) while the grid still has a few blocks per SM
+    const int64_t bx = (pl.W + kMeasureThreads - 1) / kMeasureThreads;
+    int64_t H = pl.L < kMeasureBand ? pl.L : kMeasureBand;
+    while (H % 32 == 0 && bx * ((pl.L + H - 1) / H) < 148 * 4)
+        H >>= 1;
+    const dim3 grid((unsigned)bx, (unsigned)((pl.L + H - 1) / H));
     if (pl.model == 0)
-        k_measure<0><<<grid, kMeasureThreads, 0, st>>>(pl, H, hdr, R, C, sweep);
+        k_measure<0><<<grid, kMeasureThreads, 0, st>>>(pl, (int)H, hdr, R, C, sweep);
     else
-        k_measure<1><<<grid, kMeasureThreads, 0, st>>>(pl, H, hdr, R, C, sweep);
+        k_measure<1><<<grid, kMeasureThreads, 0, st>>>(pl, (int)H, hdr, R, C, sweep);
     return cudaGetLastError();
 }
 
