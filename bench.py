@@ -134,6 +134,54 @@ def cpu_baseline(model, beta, delta, budget_s=12.0, seed=wl.BASE_SEED + 99):
                       f"{dt:.1f} s on {threads} threads"}
 
 
+def batched_bench(sweeps=10000, n_rep=4096, record_every=1000):
+    """The replica-ensemble workload: n_rep independent Ising replicas, L drawn
+    uniformly from {64, 128, 256, 512, 1024}, hot start quenched to beta_c,
+    `sweeps` sweeps in one persistent graph-captured launch (records every
+    `record_every` sweeps), against one L = 32768 lattice (about the same
+    number of spins) swept alone."""
+    import torch
+
+    import paper_2503_14688_b300 as P
+
+    Ls = wl.ensemble_sizes(n_rep)
+    seeds = [wl.BASE_SEED + 3 + r for r in range(n_rep)]
+    stream = torch.cuda.Stream()
+    ens = P.Ensemble(Ls, seeds, stream=stream, record_capacity=sweeps // record_every + 1)
+    ens.init_random()
+    threads = ens.autotune(4)
+    ens.sweep(4, beta=wl.BETA_C_ISING)  # warm-up (graph instantiation)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    ens.sweep(sweeps, beta=wl.BETA_C_ISING, record_every=record_every)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b)
+    spins = float(np.sum(Ls.astype(np.float64) ** 2))
+    rows = ens.read_records(with_sums=False)
+    ens.close()
+    batched = spins * sweeps / (ms * 1e6)
+    # one lattice of about the same number of spins
+    Ls1, n1 = 32768, 200
+    lat = P.Lattice(Ls1, wl.ISING, seed=wl.BASE_SEED + 3, stream=stream)
+    lat.init_random()
+    lat.sweep(3, beta=wl.BETA_C_ISING)
+    torch.cuda.synchronize()
+    a.record(stream)
+    lat.sweep(n1, beta=wl.BETA_C_ISING)
+    b.record(stream)
+    torch.cuda.synchronize()
+    single = float(Ls1) ** 2 * n1 / (a.elapsed_time(b) * 1e6)
+    lat.close()
+    return {"workload": f"{n_rep} Ising replicas, L uniform in {{64..1024}}, beta_c, "
+                        f"{sweeps} sweeps in one persistent launch, records every {record_every}",
+            "value": batched, "unit": UNIT, "ms": ms, "spins": spins, "record_rows": len(rows),
+            "threads_per_cta": threads,
+            "single_lattice_equal_spins": {"L": Ls1, "value": single, "unit": UNIT},
+            "ratio_vs_single": batched / single}
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -275,6 +323,8 @@ def run_ours(args, w):
             "clocks": clk,
             "xi2_last": xi,
         }
+        if not args.no_batched and world == 1:
+            line["batched"] = batched_bench()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w.model, beta, w.delta)
         print(json.dumps(line), flush=True)
@@ -291,6 +341,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ising_large")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the replica-ensemble measurement")
     ap.add_argument("--L", type=int, default=0, help="override the workload's L (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -220,6 +220,65 @@ isg_status isg_measure_planes_noalloc(int32_t model, int64_t L, const void *d_pl
  * <S0> <= <Sk> or an argument is invalid; +inf if <Sk> = 0 < <S0>. */
 double isg_xi2(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const int32_t *C);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles: many independent replicas (the replica averages of Eqs. (2)-(3)
+ * and Appendix B), of uneven L and models, swept together.  Replicas that fit
+ * in shared memory (Ising L <= 1280, Blume-Capel L <= 896) are run by one
+ * persistent kernel -- each CTA takes whole replicas from a work counter,
+ * largest first, and keeps them in shared memory for all sweeps of a call;
+ * larger replicas are swept by the single-lattice kernels on the same stream.
+ * Replica r evolves bit for bit like a lattice created alone with seed[r].
+ * ------------------------------------------------------------------------- */
+typedef struct isg_ensemble isg_ensemble;
+
+typedef struct {
+    int64_t n;               /* number of replicas (>= 1)                        */
+    const int64_t *L;        /* n sides (valid L as for lattices)                */
+    const int32_t *model;    /* n models, or NULL for all Ising                  */
+    const uint64_t *seed;    /* n Philox keys                                    */
+    double delta;            /* Blume-Capel crystal field, shared                */
+    void *stream;            /* cudaStream_t; NULL = an internal stream          */
+    int64_t record_capacity; /* record rows kept on the device (>= 1); a row
+                                holds one record per replica (32 + 8 L_r bytes) */
+} isg_ensemble_desc;
+
+/* Allocate all replicas' planes and the record ring; spins undefined. */
+isg_status isg_ensemble_create(const isg_ensemble_desc *desc, isg_ensemble **out);
+
+/* Release everything (waits for the stream).  NULL is accepted. */
+void isg_ensemble_destroy(isg_ensemble *ens);
+
+/* Hot start of every replica (as isg_lattice_init_random with seed[r]);
+ * sweep counter 0, records dropped. */
+isg_status isg_ensemble_init_random(isg_ensemble *ens);
+
+/* n sweeps of every replica at betas[i] (n host doubles) or beta_const; with
+ * record_every = k > 0 one record row after every k-th sweep of the call
+ * (ISG_ERR_BUSY if the ring lacks room).  The device work of the call (the
+ * threshold upload, one persistent launch, the large replicas' launches) is
+ * captured in a CUDA graph, instantiated once and updated in place by later
+ * calls of the same shape.  Asynchronous. */
+isg_status isg_ensemble_sweep(isg_ensemble *ens, int64_t n, const double *betas,
+                              double beta_const, int64_t record_every);
+
+/* Move up to `rows` oldest record rows into out[i*n + r] (replica r of row
+ * i): scalars, and row/column sums into the host arrays out[] points to (if
+ * not NULL; L_r int32 each).  *count = rows moved.  Synchronises. */
+isg_status isg_ensemble_read_records(isg_ensemble *ens, int64_t rows, isg_obs *out,
+                                     int64_t *count);
+
+/* Replica r's lattice as L_r * L_r host bytes (row-major).  Synchronises. */
+isg_status isg_ensemble_get(isg_ensemble *ens, int64_t r, int8_t *out);
+
+/* Replicas, sweeps done, pending record rows, threads per CTA in use. */
+isg_status isg_ensemble_info(const isg_ensemble *ens, int64_t *n, int64_t *sweep,
+                             int64_t *pending, int32_t *threads_per_cta);
+
+/* Pick the CTA size of the persistent kernel (256, 512 or 1024 threads) by
+ * timing `sweeps` sweeps of each on a copy of the replicas (their state is
+ * not changed).  *threads_out (may be NULL) = the choice.  Synchronises. */
+isg_status isg_ensemble_autotune(isg_ensemble *ens, int64_t sweeps, int32_t *threads_out);
+
 /* Energy per spin (-B + Delta Q) / L^2 of one record. */
 double isg_energy_density(const isg_obs *obs, int64_t L, double delta);
 

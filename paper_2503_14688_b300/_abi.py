@@ -38,6 +38,13 @@ class isg_obs(ctypes.Structure):
                 ("col_sums", ctypes.POINTER(ctypes.c_int32))]
 
 
+class isg_ensemble_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("L", ctypes.POINTER(ctypes.c_int64)),
+                ("model", ctypes.POINTER(ctypes.c_int32)), ("seed", ctypes.POINTER(ctypes.c_uint64)),
+                ("delta", ctypes.c_double), ("stream", ctypes.c_void_p),
+                ("record_capacity", ctypes.c_int64)]
+
+
 class isg_schedule(ctypes.Structure):
     _fields_ = [("n_pieces", ctypes.c_int64), ("t_start", ctypes.POINTER(ctypes.c_int64)),
                 ("beta", ctypes.POINTER(ctypes.c_double))]
@@ -73,6 +80,14 @@ PROTOTYPES = {
     "isg_xi2": (_F64, [_I64, _I64, _I64P, _I32P, _I32P]),
     "isg_energy_density": (_F64, [ctypes.POINTER(isg_obs), _I64, _F64]),
     "isg_last_error": (ctypes.c_char_p, []),
+    "isg_ensemble_create": (_I32, [ctypes.POINTER(isg_ensemble_desc), ctypes.POINTER(_P)]),
+    "isg_ensemble_destroy": (None, [_P]),
+    "isg_ensemble_init_random": (_I32, [_P]),
+    "isg_ensemble_sweep": (_I32, [_P, _I64, _F64P, _F64, _I64]),
+    "isg_ensemble_read_records": (_I32, [_P, _I64, ctypes.POINTER(isg_obs), _I64P]),
+    "isg_ensemble_get": (_I32, [_P, _I64, _I8P]),
+    "isg_ensemble_info": (_I32, [_P, _I64P, _I64P, _I64P, _I32P]),
+    "isg_ensemble_autotune": (_I32, [_P, _I64, _I32P]),
 }
 
 _lib = None

@@ -1,0 +1,866 @@
+// isg_ensemble.cu -- many independent replicas of uneven L in one persistent,
+// graph-captured launch (the replica averages <...> of Eqs. (2)-(3) and
+// Appendix B need thousands of independent realisations of a protocol).
+//
+// Each CTA of a persistent grid (one or more per SM) takes replicas from a
+// global work counter, largest L first, copies the replica's spin planes
+// into shared memory (an Ising L = 1024 lattice is 128 KiB), runs all sweeps
+// of the launch there -- a __syncthreads between half-sweeps, no wait on any
+// other CTA -- records observables into the ensemble's record ring, and
+// writes the planes back.  The per-site keying is the one of the single
+// lattice path, so replica r evolves bit for bit as a lattice created alone
+// with the same seed.  Replicas too large for shared memory are swept by the
+// global-memory kernels, one after another, on the same stream.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "isg.h"
+#include "isg_internal.h"
+#include "isg_philox.cuh"
+#include "isg_sweep_core.cuh"
+
+using namespace isg;
+
+namespace {
+
+constexpr int kMaxSmemBytes = 227 * 1024;
+constexpr int kCounterBits = 8;  // column counters in the shared-memory measure
+
+struct EnsItem {
+    uint64_t seed;
+    uint32_t *planes;     // the replica's planes in global memory
+    uint64_t rec_offset;  // byte offset of its record inside a record row
+    int32_t L;
+    int32_t model;
+};
+
+struct EnsArgs {
+    const EnsItem *items;
+    const int32_t *order;  // replica indices, shared-memory path, largest first
+    int32_t n_order;
+    int32_t *counter;      // work counter, zero at launch
+    const IsingThr *ithr;  // per sweep of this launch
+    const BcTable *btab;   // per sweep of this launch (Blume-Capel), may be null
+    uint8_t *rec_ring;
+    uint64_t row_bytes;
+    int32_t rec_cap;
+    int32_t rec_row0;      // ring row of this launch's first record
+    uint32_t t0;
+    int32_t nsweeps;
+    int32_t record_every;
+};
+
+size_t smem_bytes_for(int32_t model, int64_t L)
+{
+    const size_t planes = (size_t)L * (size_t)L / (model == ISG_ISING ? 8 : 4);
+    return planes + 8 * (size_t)L + 4 * kBcTableSize + 64;
+}
+
+// ---------------------------------------------------------------------------
+// Observables of the replica held in shared memory (after a full sweep).
+// ---------------------------------------------------------------------------
+template <int MODEL>
+__device__ void smem_measure(const uint32_t *P, int L, int W, int32_t *R_s, int32_t *C_s,
+                             unsigned long long *acc, uint8_t *rec, int64_t sweep)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int LW = L * W;
+    for (int i = tid; i < L; i += nt) {
+        R_s[i] = 0;
+        C_s[i] = 0;
+    }
+    if (tid < 3)
+        acc[tid] = 0;
+    __syncthreads();
+    const uint32_t *p0 = MODEL == 0 ? P : P + LW;
+    const uint32_t *p1 = MODEL == 0 ? P + LW : P + 3 * LW;
+    const uint32_t *n0 = P, *n1 = P + 2 * LW;
+    int b = 0, m = 0, q = 0;
+    // bonds, magnetisation, row sums: one colour-1 word with its colour-0 neighbours
+    for (int i = tid; i < LW; i += nt) {
+        const int y = i / W, w = i - y * W;
+        const int yu = y == 0 ? L - 1 : y - 1, yd = y + 1 == L ? 0 : y + 1;
+        const int par = (1 ^ y) & 1;
+        const int ew = par == 0 ? (w == 0 ? W - 1 : w - 1) : (w + 1 == W ? 0 : w + 1);
+        const uint32_t Tp = p1[i], Sp = p0[i];
+        const uint32_t Xp = side_word(Sp, p0[y * W + ew], par);
+        const uint32_t Up = p0[yu * W + w], Dp = p0[yd * W + w];
+        int rp;
+        if (MODEL == 0) {
+            const int anti = __popc(Tp ^ Up) + __popc(Tp ^ Dp) + __popc(Tp ^ Sp) + __popc(Tp ^ Xp);
+            b += 128 - 2 * anti;
+            rp = 2 * (__popc(Tp) + __popc(Sp)) - 64;
+        } else {
+            const uint32_t Tn = n1[i], Sn = n0[i];
+            const uint32_t Xn = side_word(Sn, n0[y * W + ew], par);
+            const uint32_t nb[4] = {n0[yu * W + w], n0[yd * W + w], Sn, Xn};
+            const uint32_t pb[4] = {Up, Dp, Sp, Xp};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t both = Tn & nb[k];
+                b += __popc(both) - 2 * __popc(both & (Tp ^ pb[k]));
+            }
+            rp = __popc(Tn & Tp) + __popc(Sn & Sp) - __popc(Tn & ~Tp) - __popc(Sn & ~Sp);
+            q += __popc(Tn) + __popc(Sn);
+        }
+        m += rp;
+        atomicAdd(&R_s[y], rp);
+    }
+    if (MODEL == 0)
+        q = 0;
+    b = __reduce_add_sync(0xFFFFFFFFu, b);
+    m = __reduce_add_sync(0xFFFFFFFFu, m);
+    q = __reduce_add_sync(0xFFFFFFFFu, q);
+    if ((tid & 31) == 0) {
+        atomicAdd(&acc[0], (unsigned long long)(long long)b);
+        atomicAdd(&acc[1], (unsigned long long)(long long)m);
+        atomicAdd(&acc[2], (unsigned long long)(long long)q);
+    }
+    // column sums: thread (g, w) counts rows [g R_g, (g+1) R_g) of word column w
+    const int G = nt / W > 0 ? nt / W : 1;
+    const int Rg = (L + G - 1) / G;
+    if (tid < G * W) {
+        const int g = tid / W, w = tid - g * W;
+        const int ya = g * Rg, yb = min(L, ya + Rg);
+        uint32_t ep[kCounterBits] = {}, op[kCounterBits] = {};
+        uint32_t em[kCounterBits] = {}, om[kCounterBits] = {};
+        for (int y = ya; y < yb; ++y) {
+            const bool odd = y & 1;
+            uint32_t e_p, o_p, e_m = 0, o_m = 0;
+            if (MODEL == 0) {
+                e_p = odd ? p1[y * W + w] : p0[y * W + w];
+                o_p = odd ? p0[y * W + w] : p1[y * W + w];
+            } else {
+                const uint32_t a_n = n0[y * W + w], a_p = p0[y * W + w];
+                const uint32_t c_n = n1[y * W + w], c_p = p1[y * W + w];
+                const uint32_t plus0 = a_n & a_p, minus0 = a_n & ~a_p;
+                const uint32_t plus1 = c_n & c_p, minus1 = c_n & ~c_p;
+                e_p = odd ? plus1 : plus0;
+                o_p = odd ? plus0 : plus1;
+                e_m = odd ? minus1 : minus0;
+                o_m = odd ? minus0 : minus1;
+            }
+            uint32_t x;
+            x = e_p;
+            for (int l = 0; l < kCounterBits && x; ++l) { const uint32_t c = ep[l] & x; ep[l] ^= x; x = c; }
+            x = o_p;
+            for (int l = 0; l < kCounterBits && x; ++l) { const uint32_t c = op[l] & x; op[l] ^= x; x = c; }
+            if (MODEL == 1) {
+                x = e_m;
+                for (int l = 0; l < kCounterBits && x; ++l) { const uint32_t c = em[l] & x; em[l] ^= x; x = c; }
+                x = o_m;
+                for (int l = 0; l < kCounterBits && x; ++l) { const uint32_t c = om[l] & x; om[l] ^= x; x = c; }
+            }
+        }
+        const int rows = yb > ya ? yb - ya : 0;
+        for (int bit = 0; bit < 32; ++bit) {
+            int ce = 0, co = 0, cem = 0, com = 0;
+#pragma unroll
+            for (int l = 0; l < kCounterBits; ++l) {
+                ce |= (int)((ep[l] >> bit) & 1u) << l;
+                co |= (int)((op[l] >> bit) & 1u) << l;
+                if (MODEL == 1) {
+                    cem |= (int)((em[l] >> bit) & 1u) << l;
+                    com |= (int)((om[l] >> bit) & 1u) << l;
+                }
+            }
+            const int x = 2 * (32 * w + bit);
+            const int ve = MODEL == 0 ? 2 * ce - rows : ce - cem;
+            const int vo = MODEL == 0 ? 2 * co - rows : co - com;
+            if (ve)
+                atomicAdd(&C_s[x], ve);
+            if (vo)
+                atomicAdd(&C_s[x + 1], vo);
+        }
+    }
+    __syncthreads();
+    int64_t *hdr = reinterpret_cast<int64_t *>(rec);
+    int32_t *R = reinterpret_cast<int32_t *>(rec + 32);
+    int32_t *C = R + L;
+    if (tid == 0) {
+        hdr[0] = sweep;
+        hdr[1] = (int64_t)acc[0];
+        hdr[2] = (int64_t)acc[1];
+        hdr[3] = MODEL == 0 ? (int64_t)L * L : (int64_t)acc[2];
+    }
+    for (int i = tid; i < L; i += nt) {
+        R[i] = R_s[i];
+        C[i] = C_s[i];
+    }
+    __syncthreads();
+}
+
+template <int MODEL>
+__device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
+{
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int L = it.L, W = L / 64, LW = L * W;
+    const int nplanes = MODEL == 0 ? 2 : 4;
+    uint32_t *P = smem;
+    int32_t *R_s = reinterpret_cast<int32_t *>(P + nplanes * LW);
+    int32_t *C_s = R_s + L;
+    uint32_t *s_thr = reinterpret_cast<uint32_t *>(C_s + L);
+    unsigned long long *acc = reinterpret_cast<unsigned long long *>(s_thr + kBcTableSize);
+
+    const uint4 *g4 = reinterpret_cast<const uint4 *>(it.planes);
+    uint4 *s4 = reinterpret_cast<uint4 *>(P);
+    for (int i = tid; i < nplanes * LW / 4; i += nt)
+        s4[i] = g4[i];
+    __syncthreads();
+
+    const int dy = nt / W, dw = nt - (nt / W) * W;
+    const uint64_t qrow = (uint64_t)(L / 8);
+    for (int s = 0; s < a.nsweeps; ++s) {
+        const uint32_t t = a.t0 + (uint32_t)s;
+        if (MODEL == 1) {
+            for (int i = tid; i < kBcTableSize; i += nt)
+                s_thr[i] = a.btab[s].thr[i];
+            __syncthreads();
+        }
+        for (int c = 0; c < 2; ++c) {
+            const PhiloxLaunch pc = philox_consts_device(it.seed, t, (uint32_t)c);
+            int y = tid / W, w = tid - (tid / W) * W;
+            if (MODEL == 0) {
+                const IsingThr thr = a.ithr[s];
+                const uint32_t *nb = P + (1 - c) * LW;
+                uint32_t *tg = P + c * LW;
+                while (y < L) {
+                    const int yu = y == 0 ? L - 1 : y - 1, yd = y + 1 == L ? 0 : y + 1;
+                    const int par = (c ^ y) & 1;
+                    const int ew = par == 0 ? (w == 0 ? W - 1 : w - 1) : (w + 1 == W ? 0 : w + 1);
+                    const uint32_t same = nb[y * W + w];
+                    const uint32_t X = side_word(same, nb[y * W + ew], par);
+                    const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)w;
+                    tg[y * W + w] = ising_word_update(tg[y * W + w], nb[yu * W + w], nb[yd * W + w],
+                                                      same, X, q0, pc, thr);
+                    w += dw;
+                    y += dy;
+                    if (w >= W) {
+                        w -= W;
+                        ++y;
+                    }
+                }
+            } else {
+                const uint32_t *nbn = P + 2 * (1 - c) * LW, *nbp = nbn + LW;
+                uint32_t *tn = P + 2 * c * LW, *tp = tn + LW;
+                while (y < L) {
+                    const int yu = y == 0 ? L - 1 : y - 1, yd = y + 1 == L ? 0 : y + 1;
+                    const int par = (c ^ y) & 1;
+                    const int ew = par == 0 ? (w == 0 ? W - 1 : w - 1) : (w + 1 == W ? 0 : w + 1);
+                    const uint32_t sn = nbn[y * W + w], sp = nbp[y * W + w];
+                    const uint32_t nn[4] = {nbn[yu * W + w], nbn[yd * W + w], sn,
+                                            side_word(sn, nbn[y * W + ew], par)};
+                    const uint32_t pp[4] = {nbp[yu * W + w], nbp[yd * W + w], sp,
+                                            side_word(sp, nbp[y * W + ew], par)};
+                    uint32_t n = tn[y * W + w], p = tp[y * W + w];
+                    const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)w;
+                    bc_word_update(n, p, nn, pp, q0, pc, s_thr);
+                    tn[y * W + w] = n;
+                    tp[y * W + w] = p;
+                    w += dw;
+                    y += dy;
+                    if (w >= W) {
+                        w -= W;
+                        ++y;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (a.record_every > 0 && (s + 1) % a.record_every == 0) {
+            const int k = (s + 1) / a.record_every - 1;
+            const int row = (a.rec_row0 + k) % a.rec_cap;
+            uint8_t *rec = a.rec_ring + (uint64_t)row * a.row_bytes + it.rec_offset;
+            smem_measure<MODEL>(P, L, W, R_s, C_s, acc, rec, (int64_t)t + 1);
+        }
+    }
+    uint4 *o4 = reinterpret_cast<uint4 *>(it.planes);
+    for (int i = tid; i < nplanes * LW / 4; i += nt)
+        o4[i] = s4[i];
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(1024, 1) k_ensemble(const EnsArgs *__restrict__ args)
+{
+    extern __shared__ __align__(16) uint32_t smem[];
+    __shared__ int s_item;
+    const EnsArgs a = *args;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_item = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= a.n_order)
+            break;
+        const EnsItem it = a.items[a.order[item]];
+        if (it.model == 0)
+            run_replica<0>(it, a, smem);
+        else
+            run_replica<1>(it, a, smem);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+isg_status efail(isg_status code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    return isg::report_error(code, "%s", buf);
+}
+
+isg_status ecuda(cudaError_t e, const char *what)
+{
+    cudaGetLastError();
+    if (e == cudaErrorMemoryAllocation)
+        return efail(ISG_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    return efail(ISG_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define ECUDA(call, what)                                                                     \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return ecuda(e_, what);                                                           \
+    } while (0)
+
+}  // namespace
+
+struct isg_ensemble {
+    int64_t n = 0;
+    std::vector<int64_t> L;
+    std::vector<int32_t> model;
+    std::vector<uint64_t> seed;
+    double delta = 0.0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    uint8_t *planes = nullptr;
+    std::vector<uint64_t> plane_off;
+    std::vector<uint64_t> rec_off;
+    EnsItem *d_items = nullptr;
+    int32_t *d_order = nullptr;
+    int32_t n_smem = 0;
+    std::vector<int64_t> global_list;
+    int32_t *d_counter = nullptr;
+    EnsArgs *d_args = nullptr;
+    EnsArgs *h_args = nullptr;  // pinned
+    IsingThr *d_ithr = nullptr, *h_ithr = nullptr;
+    BcTable *d_btab = nullptr, *h_btab = nullptr;
+    int64_t thr_cap = 0;
+    bool any_bc = false;
+    uint8_t *rec_ring = nullptr;
+    uint64_t row_bytes = 0;
+    int64_t rec_cap = 0, rec_head = 0, rec_count = 0;
+    int64_t t = 0;
+    int threads = 1024;
+    int blocks = 0;
+    size_t smem = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+void free_tables(isg_ensemble *e)
+{
+    if (e->d_ithr) cudaFree(e->d_ithr);
+    if (e->h_ithr) cudaFreeHost(e->h_ithr);
+    if (e->d_btab) cudaFree(e->d_btab);
+    if (e->h_btab) cudaFreeHost(e->h_btab);
+    e->d_ithr = e->h_ithr = nullptr;
+    e->d_btab = e->h_btab = nullptr;
+    e->thr_cap = 0;
+}
+
+isg_status ensure_tables(isg_ensemble *e, int64_t n)
+{
+    if (n <= e->thr_cap)
+        return ISG_OK;
+    cudaStreamSynchronize(e->stream);
+    free_tables(e);
+    const int64_t cap = std::max<int64_t>(n, 64);
+    ECUDA(cudaMalloc(&e->d_ithr, sizeof(IsingThr) * cap), "threshold table");
+    ECUDA(cudaMallocHost(&e->h_ithr, sizeof(IsingThr) * cap), "threshold table (host)");
+    if (e->any_bc) {
+        ECUDA(cudaMalloc(&e->d_btab, sizeof(BcTable) * cap), "threshold table");
+        ECUDA(cudaMallocHost(&e->h_btab, sizeof(BcTable) * cap), "threshold table (host)");
+    }
+    e->thr_cap = cap;
+    return ISG_OK;
+}
+
+Planes replica_planes(const isg_ensemble *e, int64_t r)
+{
+    Planes p;
+    p.base = reinterpret_cast<uint32_t *>(e->planes + e->plane_off[r]);
+    p.L = e->L[r];
+    p.W = e->L[r] / 64;
+    p.model = e->model[r];
+    return p;
+}
+
+int occupancy_blocks(int threads, size_t smem)
+{
+    int dev = 0, sms = 148, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_ensemble, threads, smem);
+    if (per_sm < 1)
+        per_sm = 1;
+    return sms * per_sm;
+}
+
+// Queue one launch of the shared-memory kernel over all its replicas plus
+// the global-memory sweeps of the large replicas, for sweeps t .. t+n-1.
+isg_status queue_sweeps(isg_ensemble *e, int64_t n, int64_t record_every, int64_t rec_row0)
+{
+    cudaStream_t st = e->stream;
+    if (e->n_smem > 0 && n > 0) {
+        EnsArgs &a = *e->h_args;
+        a.items = e->d_items;
+        a.order = e->d_order;
+        a.n_order = e->n_smem;
+        a.counter = e->d_counter;
+        a.ithr = e->d_ithr;
+        a.btab = e->d_btab;
+        a.rec_ring = e->rec_ring;
+        a.row_bytes = e->row_bytes;
+        a.rec_cap = (int32_t)e->rec_cap;
+        a.rec_row0 = (int32_t)rec_row0;
+        a.t0 = (uint32_t)e->t;
+        a.nsweeps = (int32_t)n;
+        a.record_every = (int32_t)record_every;
+        ECUDA(cudaMemcpyAsync(e->d_args, e->h_args, sizeof(EnsArgs), cudaMemcpyHostToDevice, st),
+              "ensemble args");
+        ECUDA(cudaMemsetAsync(e->d_counter, 0, sizeof(int32_t), st), "work counter");
+        k_ensemble<<<e->blocks, e->threads, e->smem, st>>>(e->d_args);
+        ECUDA(cudaGetLastError(), "ensemble launch");
+    }
+    for (int64_t r : e->global_list) {
+        const Planes pl = replica_planes(e, r);
+        for (int64_t i = 0; i < n; ++i) {
+            const uint32_t t = (uint32_t)(e->t + i);
+            for (int c = 0; c < 2; ++c) {
+                PhiloxLaunch ph;
+                philox_launch_consts(e->seed[r], t, (uint32_t)c, &ph);
+                ECUDA(launch_half_sweep(pl, c, ph, e->h_ithr[i], e->h_btab ? &e->h_btab[i] : nullptr, st),
+                      "half-sweep launch");
+            }
+            if (record_every > 0 && (i + 1) % record_every == 0) {
+                const int64_t row = (rec_row0 + (i + 1) / record_every - 1) % e->rec_cap;
+                uint8_t *rec = e->rec_ring + (uint64_t)row * e->row_bytes + e->rec_off[r];
+                ECUDA(cudaMemsetAsync(rec, 0, record_stride(e->L[r]), st), "record clear");
+                ECUDA(launch_measure(pl, rec, (int64_t)t + 1, st), "measure launch");
+            }
+        }
+    }
+    return ISG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+isg_status isg_ensemble_create(const isg_ensemble_desc *d, isg_ensemble **out)
+{
+    if (out)
+        *out = nullptr;
+    if (!d || !out || d->n < 1 || !d->L || !d->seed || d->record_capacity < 1)
+        return efail(ISG_ERR_INVALID, "bad ensemble description");
+    if (std::isnan(d->delta) || std::isinf(d->delta))
+        return efail(ISG_ERR_INVALID, "delta must be finite");
+    for (int64_t r = 0; r < d->n; ++r) {
+        const int32_t m = d->model ? d->model[r] : ISG_ISING;
+        if (isg_lattice_bytes(m, d->L[r]) == 0)
+            return efail(ISG_ERR_INVALID, "replica %lld: invalid model %d or L %lld", (long long)r,
+                         m, (long long)d->L[r]);
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return efail(ISG_ERR_UNSUPPORTED, "no usable CUDA device");
+    }
+    isg_ensemble *e = new (std::nothrow) isg_ensemble();
+    if (!e)
+        return efail(ISG_ERR_OOM, "host allocation failed");
+    e->n = d->n;
+    e->L.assign(d->L, d->L + d->n);
+    e->seed.assign(d->seed, d->seed + d->n);
+    e->model.resize(d->n);
+    for (int64_t r = 0; r < d->n; ++r) {
+        e->model[r] = d->model ? d->model[r] : ISG_ISING;
+        e->any_bc |= e->model[r] == ISG_BLUME_CAPEL;
+    }
+    e->delta = d->delta;
+    e->rec_cap = d->record_capacity;
+    auto cleanup = [&](isg_status s) {
+        isg_ensemble_destroy(e);
+        return s;
+    };
+    if (d->stream) {
+        e->stream = (cudaStream_t)d->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return cleanup(ecuda(cudaGetLastError(), "stream"));
+        e->own_stream = true;
+    }
+    // planes: one allocation, 256-byte aligned per replica; record offsets
+    uint64_t off = 0, roff = 0;
+    e->plane_off.resize(d->n);
+    e->rec_off.resize(d->n);
+    for (int64_t r = 0; r < d->n; ++r) {
+        e->plane_off[r] = off;
+        off += (isg_lattice_bytes(e->model[r], e->L[r]) + 255) & ~(uint64_t)255;
+        e->rec_off[r] = roff;
+        roff += record_stride(e->L[r]);
+    }
+    e->row_bytes = (roff + 255) & ~(uint64_t)255;
+    cudaError_t err = cudaMalloc(&e->planes, off);
+    if (err == cudaSuccess)
+        err = cudaMalloc(&e->rec_ring, e->row_bytes * (uint64_t)e->rec_cap);
+    if (err == cudaSuccess)
+        err = cudaMalloc(&e->d_counter, sizeof(int32_t));
+    if (err == cudaSuccess)
+        err = cudaMalloc(&e->d_args, sizeof(EnsArgs));
+    if (err == cudaSuccess)
+        err = cudaMallocHost(&e->h_args, sizeof(EnsArgs));
+    if (err != cudaSuccess)
+        return cleanup(ecuda(err, "ensemble allocation"));
+    // work split: shared-memory replicas largest first; the rest global
+    std::vector<int32_t> order;
+    size_t smem = 0;
+    for (int64_t r = 0; r < d->n; ++r) {
+        const size_t need = smem_bytes_for(e->model[r], e->L[r]);
+        if (need <= (size_t)kMaxSmemBytes) {
+            order.push_back((int32_t)r);
+            smem = std::max(smem, need);
+        } else {
+            e->global_list.push_back(r);
+        }
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return e->L[a] * e->L[a] * (e->model[a] + 1) > e->L[b] * e->L[b] * (e->model[b] + 1);
+    });
+    e->n_smem = (int32_t)order.size();
+    std::vector<EnsItem> items(d->n);
+    for (int64_t r = 0; r < d->n; ++r) {
+        items[r].seed = e->seed[r];
+        items[r].planes = reinterpret_cast<uint32_t *>(e->planes + e->plane_off[r]);
+        items[r].rec_offset = e->rec_off[r];
+        items[r].L = (int32_t)e->L[r];
+        items[r].model = e->model[r];
+    }
+    err = cudaMalloc(&e->d_items, sizeof(EnsItem) * d->n);
+    if (err == cudaSuccess && !order.empty())
+        err = cudaMalloc(&e->d_order, sizeof(int32_t) * order.size());
+    if (err == cudaSuccess)
+        err = cudaMemcpy(e->d_items, items.data(), sizeof(EnsItem) * d->n, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && !order.empty())
+        err = cudaMemcpy(e->d_order, order.data(), sizeof(int32_t) * order.size(),
+                         cudaMemcpyHostToDevice);
+    if (err != cudaSuccess)
+        return cleanup(ecuda(err, "ensemble tables"));
+    e->smem = smem;
+    if (smem > 48 * 1024) {
+        err = cudaFuncSetAttribute(k_ensemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess)
+            return cleanup(ecuda(err, "shared memory opt-in"));
+    }
+    e->threads = 1024;
+    e->blocks = occupancy_blocks(e->threads, e->smem);
+    *out = e;
+    return ISG_OK;
+}
+
+void isg_ensemble_destroy(isg_ensemble *e)
+{
+    if (!e)
+        return;
+    if (e->stream)
+        cudaStreamSynchronize(e->stream);
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    free_tables(e);
+    if (e->planes) cudaFree(e->planes);
+    if (e->rec_ring) cudaFree(e->rec_ring);
+    if (e->d_counter) cudaFree(e->d_counter);
+    if (e->d_args) cudaFree(e->d_args);
+    if (e->h_args) cudaFreeHost(e->h_args);
+    if (e->d_items) cudaFree(e->d_items);
+    if (e->d_order) cudaFree(e->d_order);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+isg_status isg_ensemble_init_random(isg_ensemble *e)
+{
+    if (!e)
+        return efail(ISG_ERR_INVALID, "ensemble is NULL");
+    for (int64_t r = 0; r < e->n; ++r) {
+        PhiloxLaunch ph0, ph1;
+        philox_launch_consts(e->seed[r], 0u, 2u, &ph0);
+        philox_launch_consts(e->seed[r], 0u, 3u, &ph1);
+        ECUDA(launch_init_random(replica_planes(e, r), ph0, ph1, e->stream), "init launch");
+    }
+    e->t = 0;
+    e->rec_head = e->rec_count = 0;
+    return ISG_OK;
+}
+
+isg_status isg_ensemble_sweep(isg_ensemble *e, int64_t n, const double *betas, double beta_const,
+                              int64_t record_every)
+{
+    if (!e)
+        return efail(ISG_ERR_INVALID, "ensemble is NULL");
+    if (n < 0 || record_every < 0 || n > (int64_t)INT32_MAX)
+        return efail(ISG_ERR_INVALID, "bad n or record_every");
+    if (e->t + n > (int64_t)0xFFFFFFFFLL)
+        return efail(ISG_ERR_INVALID, "sweep index would reach 2^32");
+    const int64_t nrec = record_every > 0 ? n / record_every : 0;
+    if (e->rec_count + nrec > e->rec_cap)
+        return efail(ISG_ERR_BUSY, "record ring has room for %lld rows, %lld requested",
+                     (long long)(e->rec_cap - e->rec_count), (long long)nrec);
+    for (int64_t i = 0; i < n; ++i) {
+        const double b = betas ? betas[i] : beta_const;
+        if (std::isnan(b) || b < 0.0)
+            return efail(ISG_ERR_INVALID, "beta[%lld] = %g is not >= 0", (long long)i, b);
+    }
+    if (n == 0)
+        return ISG_OK;
+    isg_status s = ensure_tables(e, n);
+    if (s != ISG_OK)
+        return s;
+    // the pinned tables may still be read by a previous call's copies
+    ECUDA(cudaStreamSynchronize(e->stream), "stream sync");
+    for (int64_t i = 0; i < n; ++i) {
+        const double b = betas ? betas[i] : beta_const;
+        ising_thresholds(b, &e->h_ithr[i]);
+        if (e->h_btab)
+            bc_table(b, e->delta, &e->h_btab[i]);
+    }
+    const int64_t row0 = (e->rec_head + e->rec_count) % e->rec_cap;
+    // capture this call's device work in a graph and replay it; a later call
+    // with the same shape updates the instantiated graph in place
+    cudaStream_t st = e->stream;
+    ECUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t ce = cudaMemcpyAsync(e->d_ithr, e->h_ithr, sizeof(IsingThr) * n,
+                                     cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess && e->h_btab)
+        ce = cudaMemcpyAsync(e->d_btab, e->h_btab, sizeof(BcTable) * n, cudaMemcpyHostToDevice, st);
+    isg_status qs = ce == cudaSuccess ? queue_sweeps(e, n, record_every, row0) : ISG_OK;
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(st, &g);
+    if (ce != cudaSuccess || qs != ISG_OK || ee != cudaSuccess) {
+        if (g)
+            cudaGraphDestroy(g);
+        if (qs != ISG_OK)
+            return qs;
+        return ecuda(ce != cudaSuccess ? ce : ee, "graph capture");
+    }
+    bool updated = false;
+    if (e->exec) {
+        cudaGraphExecUpdateResultInfo info;
+        updated = cudaGraphExecUpdate(e->exec, g, &info) == cudaSuccess;
+        if (!updated) {
+            cudaGetLastError();
+            cudaGraphExecDestroy(e->exec);
+            e->exec = nullptr;
+        }
+    }
+    if (!updated) {
+        const cudaError_t ie = cudaGraphInstantiate(&e->exec, g, 0);
+        if (ie != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return ecuda(ie, "graph instantiate");
+        }
+    }
+    if (e->graph)
+        cudaGraphDestroy(e->graph);
+    e->graph = g;
+    ECUDA(cudaGraphLaunch(e->exec, st), "graph launch");
+    e->t += n;
+    e->rec_count += nrec;
+    return ISG_OK;
+}
+
+isg_status isg_ensemble_read_records(isg_ensemble *e, int64_t rows, isg_obs *out, int64_t *count)
+{
+    if (count)
+        *count = 0;
+    if (!e || !out || !count || rows < 0)
+        return efail(ISG_ERR_INVALID, "bad arguments");
+    ECUDA(cudaStreamSynchronize(e->stream), "stream sync");
+    const int64_t k = std::min(rows, e->rec_count);
+    std::vector<uint8_t> buf(e->row_bytes);
+    for (int64_t i = 0; i < k; ++i) {
+        ECUDA(cudaMemcpy(buf.data(), e->rec_ring + (uint64_t)e->rec_head * e->row_bytes, e->row_bytes,
+                         cudaMemcpyDeviceToHost),
+              "record read");
+        for (int64_t r = 0; r < e->n; ++r) {
+            const uint8_t *rec = buf.data() + e->rec_off[r];
+            int64_t hdr[4];
+            memcpy(hdr, rec, sizeof(hdr));
+            isg_obs &o = out[i * e->n + r];
+            o.sweep = hdr[0];
+            o.B = hdr[1];
+            o.M = hdr[2];
+            o.Q = hdr[3];
+            if (o.row_sums)
+                memcpy(o.row_sums, rec + 32, sizeof(int32_t) * e->L[r]);
+            if (o.col_sums)
+                memcpy(o.col_sums, rec + 32 + sizeof(int32_t) * e->L[r], sizeof(int32_t) * e->L[r]);
+        }
+        e->rec_head = (e->rec_head + 1) % e->rec_cap;
+        e->rec_count -= 1;
+        *count = i + 1;
+    }
+    return ISG_OK;
+}
+
+isg_status isg_ensemble_info(const isg_ensemble *e, int64_t *n, int64_t *sweep, int64_t *pending,
+                             int32_t *threads_per_cta)
+{
+    if (!e)
+        return efail(ISG_ERR_INVALID, "ensemble is NULL");
+    if (n)
+        *n = e->n;
+    if (sweep)
+        *sweep = e->t;
+    if (pending)
+        *pending = e->rec_count;
+    if (threads_per_cta)
+        *threads_per_cta = e->threads;
+    return ISG_OK;
+}
+
+isg_status isg_ensemble_get(isg_ensemble *e, int64_t r, int8_t *out)
+{
+    if (!e || !out || r < 0 || r >= e->n)
+        return efail(ISG_ERR_INVALID, "bad arguments");
+    const Planes pl = replica_planes(e, r);
+    const size_t nbytes = (size_t)pl.L * (size_t)pl.L;
+    int8_t *d = nullptr;
+    ECUDA(cudaMallocAsync(&d, nbytes, e->stream), "staging allocation");
+    cudaError_t err = launch_unpack_rect(pl, 0, 0, pl.L, pl.L, d, e->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(out, d, nbytes, cudaMemcpyDeviceToHost, e->stream);
+    cudaFreeAsync(d, e->stream);
+    if (err == cudaSuccess)
+        err = cudaStreamSynchronize(e->stream);
+    if (err != cudaSuccess)
+        return ecuda(err, "replica read");
+    return ISG_OK;
+}
+
+isg_status isg_ensemble_autotune(isg_ensemble *e, int64_t sweeps, int32_t *threads_out)
+{
+    if (!e || sweeps < 1)
+        return efail(ISG_ERR_INVALID, "bad arguments");
+    if (e->n_smem == 0) {
+        if (threads_out)
+            *threads_out = e->threads;
+        return ISG_OK;
+    }
+    // time the shared-memory kernel on a copy of the planes, so that the
+    // ensemble's own state does not move
+    isg_status s = ensure_tables(e, sweeps);
+    if (s != ISG_OK)
+        return s;
+    ECUDA(cudaStreamSynchronize(e->stream), "stream sync");
+    for (int64_t i = 0; i < sweeps; ++i)
+        ising_thresholds(0.44068679350977147, &e->h_ithr[i]);
+    if (e->h_btab)
+        for (int64_t i = 0; i < sweeps; ++i)
+            bc_table(0.59, e->delta, &e->h_btab[i]);
+    size_t total = 0;
+    for (int64_t r = 0; r < e->n; ++r)
+        total = std::max<size_t>(total, e->plane_off[r] + isg_lattice_bytes(e->model[r], e->L[r]));
+    uint8_t *copy = nullptr;
+    EnsItem *items = nullptr;
+    ECUDA(cudaMalloc(&copy, total), "autotune copy");
+    cudaError_t err = cudaMalloc(&items, sizeof(EnsItem) * e->n);
+    std::vector<EnsItem> h(e->n);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(h.data(), e->d_items, sizeof(EnsItem) * e->n, cudaMemcpyDeviceToHost);
+    for (int64_t r = 0; r < e->n && err == cudaSuccess; ++r)
+        h[r].planes = reinterpret_cast<uint32_t *>(copy + e->plane_off[r]);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(items, h.data(), sizeof(EnsItem) * e->n, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(copy, e->planes, total, cudaMemcpyDeviceToDevice);
+    if (err == cudaSuccess)
+        err = cudaMemcpy(e->d_ithr, e->h_ithr, sizeof(IsingThr) * sweeps, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess && e->h_btab)
+        err = cudaMemcpy(e->d_btab, e->h_btab, sizeof(BcTable) * sweeps, cudaMemcpyHostToDevice);
+    int best = e->threads;
+    float best_ms = 1e30f;
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (err == cudaSuccess)
+        err = cudaEventCreate(&a);
+    if (err == cudaSuccess)
+        err = cudaEventCreate(&b);
+    const int candidates[3] = {256, 512, 1024};
+    for (int ci = 0; ci < 3 && err == cudaSuccess; ++ci) {
+        const int nt = candidates[ci];
+        EnsArgs args{};
+        args.items = items;
+        args.order = e->d_order;
+        args.n_order = e->n_smem;
+        args.counter = e->d_counter;
+        args.ithr = e->d_ithr;
+        args.btab = e->d_btab;
+        args.rec_ring = e->rec_ring;
+        args.row_bytes = e->row_bytes;
+        args.rec_cap = (int32_t)e->rec_cap;
+        args.t0 = 0;
+        args.nsweeps = (int32_t)sweeps;
+        args.record_every = 0;
+        *e->h_args = args;
+        err = cudaMemcpy(e->d_args, e->h_args, sizeof(EnsArgs), cudaMemcpyHostToDevice);
+        const int blocks = occupancy_blocks(nt, e->smem);
+        for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {  // first run warms up
+            cudaMemsetAsync(e->d_counter, 0, sizeof(int32_t), e->stream);
+            cudaEventRecord(a, e->stream);
+            k_ensemble<<<blocks, nt, e->smem, e->stream>>>(e->d_args);
+            cudaEventRecord(b, e->stream);
+            err = cudaEventSynchronize(b);
+            float ms = 0;
+            if (err == cudaSuccess)
+                err = cudaEventElapsedTime(&ms, a, b);
+            if (err == cudaSuccess && rep == 1 && ms < best_ms) {
+                best_ms = ms;
+                best = nt;
+            }
+        }
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(copy);
+    cudaFree(items);
+    if (err != cudaSuccess)
+        return ecuda(err, "autotune");
+    e->threads = best;
+    e->blocks = occupancy_blocks(best, e->smem);
+    if (e->exec) {  // the launch shape changed: rebuild the graph next time
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+    }
+    if (threads_out)
+        *threads_out = best;
+    return ISG_OK;
+}
+
+}  // extern "C"

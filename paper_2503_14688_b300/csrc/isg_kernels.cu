@@ -24,6 +24,7 @@
 
 #include "isg_internal.h"
 #include "isg_philox.cuh"
+#include "isg_sweep_core.cuh"
 
 namespace isg {
 
@@ -183,17 +184,6 @@ __global__ void k_init_uniform(Planes pl, int value)
 // up/same/down neighbour words in registers (each neighbour word is loaded
 // once per band plus two halo rows).
 // ---------------------------------------------------------------------------
-// acc * 2 + (u >= thr): the compare is the borrow of u - thr, shifted into the
-// accumulator by an add-with-carry -- two integer instructions per compare.
-__device__ __forceinline__ uint32_t shift_in_not_below(uint32_t acc, uint32_t u, uint32_t thr)
-{
-    uint32_t out;
-    asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}"
-        : "=r"(out)
-        : "r"(u), "r"(thr), "r"(acc));
-    return out;
-}
-
 template <int V>
 __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
     k_ising_half(uint32_t *__restrict__ tgt, const uint32_t *__restrict__ nbr, int64_t L,
@@ -218,34 +208,7 @@ __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)(w0 + v);
-            const PhiloxWordPart wp = philox_word_part(pc, (uint32_t)(q0 >> 32));
-            // reject masks: bit 4i+k set iff site 4i+k's word >= the threshold
-            uint32_t r4 = 0, r8 = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                uint32_t r[4];
-                philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
-                uint32_t n4 = 0, n8 = 0;
-#pragma unroll
-                for (int k = 3; k >= 0; --k) {
-                    n4 = shift_in_not_below(n4, r[k], thr.thr4);
-                    n8 = shift_in_not_below(n8, r[k], thr.thr8);
-                }
-                r4 = n4 * (1u << (4 * i)) + r4;
-                r8 = n8 * (1u << (4 * i)) + r8;
-            }
-            const uint32_t a4 = ~r4 | thr.full4;
-            const uint32_t a8 = ~r8 | thr.full8;
-            const uint32_t t = T.v[v];
-            // anti-aligned neighbour indicators and their bit-sliced count
-            const uint32_t a = t ^ U.v[v], b = t ^ D.v[v], d = t ^ S.v[v], e = t ^ X.v[v];
-            const uint32_t s1 = a ^ b ^ d;
-            const uint32_t c1 = (a & b) | (d & (a ^ b));
-            const uint32_t s = s1 ^ e;         // count = s + 2 (c1 + c2)
-            const uint32_t c2 = s1 & e;
-            const uint32_t ge2 = c1 | c2;      // dE <= 0: always flip
-            const uint32_t flip = ge2 | (~ge2 & ((s & a4) | (~s & a8)));
-            T.v[v] = t ^ flip;
+            T.v[v] = ising_word_update(T.v[v], U.v[v], D.v[v], S.v[v], X.v[v], q0, pc, thr);
         }
         store_words<V>(tgt + y * W + w0, T);
         U = S;
@@ -260,13 +223,6 @@ __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
 // then looks its threshold up in a 128-entry table indexed by
 // (n, p, proposal bit, h + 4) held in shared memory.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &s,
-                                         uint32_t &cy)
-{
-    s = a ^ b ^ c;
-    cy = (a & b) | (c & (a ^ b));
-}
-
 template <int V>
 __global__ void __launch_bounds__(kSweepThreads)
     k_bc_half(uint32_t *__restrict__ tn_plane, uint32_t *__restrict__ tp_plane,
@@ -302,48 +258,10 @@ __global__ void __launch_bounds__(kSweepThreads)
         Words<V> Tp = load_words_rw<V>(tp_plane + y * W + w0);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-            // eight indicators: s_i = +1 (n & p), s_i != -1 (~n | p)
-            const uint32_t x0 = Un.v[v] & Up.v[v], x1 = ~Un.v[v] | Up.v[v];
-            const uint32_t x2 = Dn.v[v] & Dp.v[v], x3 = ~Dn.v[v] | Dp.v[v];
-            const uint32_t x4 = Sn.v[v] & Sp.v[v], x5 = ~Sn.v[v] | Sp.v[v];
-            const uint32_t x6 = Xn.v[v] & Xp.v[v], x7 = ~Xn.v[v] | Xp.v[v];
-            uint32_t sa, ca, sb, cb, sc, cc, g0, cd, se, ce, g1, cf;
-            full_add(x0, x1, x2, sa, ca);
-            full_add(x3, x4, x5, sb, cb);
-            full_add(sa, sb, x6, sc, cc);
-            g0 = sc ^ x7;
-            cd = sc & x7;
-            full_add(ca, cb, cc, se, ce);   // weight-2 column
-            g1 = se ^ cd;
-            cf = se & cd;
-            const uint32_t g2 = ce ^ cf;     // weight-4 column
-            const uint32_t g3 = ce & cf;     // only when h + 4 = 8
-
-            const uint32_t n = Tn.v[v], p = Tp.v[v];
+            const uint32_t nbn[4] = {Un.v[v], Dn.v[v], Sn.v[v], Xn.v[v]};
+            const uint32_t nbp[4] = {Up.v[v], Dp.v[v], Sp.v[v], Xp.v[v]};
             const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)(w0 + v);
-            const PhiloxWordPart wp = philox_word_part(pc, (uint32_t)(q0 >> 32));
-            uint32_t acc = 0, bits = 0;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                uint32_t r[4];
-                philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const int bi = 4 * i + k;
-                    const uint32_t bb = r[k] & 1u;
-                    const uint32_t idx = (((n >> bi) & 1u) << 6) | (((p >> bi) & 1u) << 5) |
-                                         (bb << 4) | (((g3 >> bi) & 1u) << 3) |
-                                         (((g2 >> bi) & 1u) << 2) | (((g1 >> bi) & 1u) << 1) |
-                                         ((g0 >> bi) & 1u);
-                    acc |= (uint32_t)((r[k] >> 1) < s_thr[idx]) << bi;
-                    bits |= bb << bi;
-                }
-            }
-            // proposed value: p' = b & ~(n & p), n' = ~n | (p ^ b)
-            const uint32_t np2 = bits & ~(n & p);
-            const uint32_t nn2 = ~n | (p ^ bits);
-            Tn.v[v] = n ^ (acc & (n ^ nn2));
-            Tp.v[v] = p ^ (acc & (p ^ np2));
+            bc_word_update(Tn.v[v], Tp.v[v], nbn, nbp, q0, pc, s_thr);
         }
         store_words<V>(tn_plane + y * W + w0, Tn);
         store_words<V>(tp_plane + y * W + w0, Tp);

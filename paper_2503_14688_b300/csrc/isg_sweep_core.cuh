@@ -1,0 +1,150 @@
+// isg_sweep_core.cuh -- the per-word Metropolis update shared by the global
+// half-sweep kernels (isg_kernels.cu) and the shared-memory ensemble kernel
+// (isg_ensemble.cu).
+//
+// A "word" is 32 same-colour sites of one row (bit b = same-colour index
+// 32 w + b).  Its four neighbour words come from the other colour's plane:
+// up (row y-1), down (row y+1), same (row y) and side (row y shifted by one
+// site; see side_word).  q0 = j0 >> 2 is the Philox counter of its first
+// site, j0 = y L/2 + 32 w; the eight Philox calls of the word use q0 .. q0+7.
+#pragma once
+
+#include <cstdint>
+
+#include "isg_internal.h"
+#include "isg_philox.cuh"
+
+namespace isg {
+
+// The side neighbour word: for parity (c ^ y) & 1 == 0 each site's other
+// horizontal neighbour is one site to the left (bit b-1, or bit 31 of the
+// previous word `edge`); for parity 1 one site to the right (bit b+1, or
+// bit 0 of the next word).
+__device__ __forceinline__ uint32_t side_word(uint32_t same, uint32_t edge, int parity)
+{
+    return parity == 0 ? (same << 1) | (edge >> 31) : (same >> 1) | (edge << 31);
+}
+
+// acc * 2 + (u >= thr): the compare is the borrow of u - thr, shifted into the
+// accumulator by an add-with-carry -- two integer instructions per compare.
+__device__ __forceinline__ uint32_t shift_in_not_below(uint32_t acc, uint32_t u, uint32_t thr)
+{
+    uint32_t out;
+    asm("{\n\t.reg .u32 d;\n\tsub.cc.u32 d, %1, %2;\n\taddc.u32 %0, %3, %3;\n\t}"
+        : "=r"(out)
+        : "r"(u), "r"(thr), "r"(acc));
+    return out;
+}
+
+// Launch-uniform Philox constants for counter words (w2, w3) -- the device
+// twin of the host's philox_launch_consts, for kernels whose key or sweep
+// index is not a launch parameter.
+__device__ __forceinline__ PhiloxLaunch philox_consts_device(uint64_t seed, uint32_t w2, uint32_t w3)
+{
+    PhiloxLaunch pc;
+    const uint32_t key0 = (uint32_t)seed, key1 = (uint32_t)(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        pc.rk0[r] = key0 + (uint32_t)r * kPhiloxW0;
+        pc.rk1[r] = key1 + (uint32_t)r * kPhiloxW1;
+    }
+    const uint64_t m1w2 = (uint64_t)kPhiloxM1 * (uint64_t)w2;
+    pc.r0_c0 = (uint32_t)(m1w2 >> 32) ^ pc.rk0[0];
+    pc.r0_c2x = w3 ^ pc.rk1[0];
+    pc.r1_c0x = (uint32_t)m1w2 ^ pc.rk0[1];
+    return pc;
+}
+
+// Ising: new target word.  A site with c anti-aligned neighbours has
+// dE = 8 - 4c (Eq. (1), J = 1): c >= 2 always flips, c = 1 flips iff
+// u < thr4, c = 0 iff u < thr8.
+__device__ __forceinline__ uint32_t ising_word_update(uint32_t t, uint32_t up, uint32_t dn,
+                                                      uint32_t same, uint32_t side, uint64_t q0,
+                                                      const PhiloxLaunch &pc, const IsingThr &thr)
+{
+    const PhiloxWordPart wp = philox_word_part(pc, (uint32_t)(q0 >> 32));
+    // reject masks: bit 4i+k set iff site 4i+k's word >= the threshold
+    uint32_t r4 = 0, r8 = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        uint32_t r[4];
+        philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
+        uint32_t n4 = 0, n8 = 0;
+#pragma unroll
+        for (int k = 3; k >= 0; --k) {
+            n4 = shift_in_not_below(n4, r[k], thr.thr4);
+            n8 = shift_in_not_below(n8, r[k], thr.thr8);
+        }
+        r4 = n4 * (1u << (4 * i)) + r4;
+        r8 = n8 * (1u << (4 * i)) + r8;
+    }
+    const uint32_t a4 = ~r4 | thr.full4;
+    const uint32_t a8 = ~r8 | thr.full8;
+    // anti-aligned neighbour indicators and their bit-sliced count
+    const uint32_t a = t ^ up, b = t ^ dn, d = t ^ same, e = t ^ side;
+    const uint32_t s1 = a ^ b ^ d;
+    const uint32_t c1 = (a & b) | (d & (a ^ b));
+    const uint32_t s = s1 ^ e;  // count = s + 2 (c1 + c2)
+    const uint32_t c2 = s1 & e;
+    const uint32_t ge2 = c1 | c2;  // dE <= 0: always flip
+    const uint32_t flip = ge2 | (~ge2 & ((s & a4) | (~s & a8)));
+    return t ^ flip;
+}
+
+__device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &s,
+                                         uint32_t &cy)
+{
+    s = a ^ b ^ c;
+    cy = (a & b) | (c & (a ^ b));
+}
+
+// Blume-Capel: new (n, p) target words.  Neighbour planes nbn/nbp hold the
+// up, down, same and side words.  The field h + 4 = #(+1 neighbours) +
+// #(neighbours != -1) is summed bit-sliced into g0..g3; each site looks its
+// threshold up in the 128-entry table s_thr (index (n, p, b, h + 4)) and
+// accepts iff (u >> 1) < entry.  Proposal: p' = b & ~(n & p),
+// n' = ~n | (p ^ b) with b = u & 1.
+__device__ __forceinline__ void bc_word_update(uint32_t &n, uint32_t &p, const uint32_t (&nbn)[4],
+                                               const uint32_t (&nbp)[4], uint64_t q0,
+                                               const PhiloxLaunch &pc, const uint32_t *s_thr)
+{
+    // eight indicators: s_i = +1 (n & p), s_i != -1 (~n | p)
+    const uint32_t x0 = nbn[0] & nbp[0], x1 = ~nbn[0] | nbp[0];
+    const uint32_t x2 = nbn[1] & nbp[1], x3 = ~nbn[1] | nbp[1];
+    const uint32_t x4 = nbn[2] & nbp[2], x5 = ~nbn[2] | nbp[2];
+    const uint32_t x6 = nbn[3] & nbp[3], x7 = ~nbn[3] | nbp[3];
+    uint32_t sa, ca, sb, cb, sc, cc, se, ce;
+    full_add(x0, x1, x2, sa, ca);
+    full_add(x3, x4, x5, sb, cb);
+    full_add(sa, sb, x6, sc, cc);
+    const uint32_t g0 = sc ^ x7, cd = sc & x7;
+    full_add(ca, cb, cc, se, ce);  // weight-2 column
+    const uint32_t g1 = se ^ cd, cf = se & cd;
+    const uint32_t g2 = ce ^ cf;  // weight-4 column
+    const uint32_t g3 = ce & cf;  // only when h + 4 = 8
+
+    const PhiloxWordPart wp = philox_word_part(pc, (uint32_t)(q0 >> 32));
+    uint32_t acc = 0, bits = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        uint32_t r[4];
+        philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int bi = 4 * i + k;
+            const uint32_t bb = r[k] & 1u;
+            const uint32_t idx = (((n >> bi) & 1u) << 6) | (((p >> bi) & 1u) << 5) | (bb << 4) |
+                                 (((g3 >> bi) & 1u) << 3) | (((g2 >> bi) & 1u) << 2) |
+                                 (((g1 >> bi) & 1u) << 1) | ((g0 >> bi) & 1u);
+            acc |= (uint32_t)((r[k] >> 1) < s_thr[idx]) << bi;
+            bits |= bb << bi;
+        }
+    }
+    const uint32_t np2 = bits & ~(n & p);
+    const uint32_t nn2 = ~n | (p ^ bits);
+    const uint32_t n_old = n, p_old = p;
+    n = n_old ^ (acc & (n_old ^ nn2));
+    p = p_old ^ (acc & (p_old ^ np2));
+}
+
+}  // namespace isg

@@ -1,0 +1,122 @@
+"""GPU parity of the replica ensemble (isg_ensemble_*): every replica must
+evolve bit for bit like a lattice swept alone with the same seed (itself
+checked against the oracle in test_gpu_parity.py), and a subset is compared
+with the oracle directly.  Sizes cover the shared-memory path (Ising
+L <= 1280, Blume-Capel L <= 896) and the global-memory path beyond it; the
+ensemble-mean xi_2 of the records is compared with the oracle's."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2503_14688_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def isg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2503_14688_b300 import build
+
+    build.build()
+    import paper_2503_14688_b300 as P
+
+    return P
+
+
+def _alone(isg, L, model, seed, betas, record_every, delta=0.0):
+    lat = isg.Lattice(L, model, seed=seed, delta=delta, record_capacity=len(betas) + 1)
+    lat.init_random()
+    lat.sweep(len(betas), betas=betas, record_every=record_every)
+    recs = lat.read_records()
+    s = lat.get()
+    lat.close()
+    return recs, s
+
+
+def _same_obs(a, b):
+    assert (a.sweep, a.B, a.M, a.Q) == (b.sweep, b.B, b.M, b.Q)
+    assert np.array_equal(a.R, b.R) and np.array_equal(a.C, b.C)
+
+
+def test_mixed_ensemble_matches_lattices_alone(isg, orc):
+    Ls = [64, 128, 192, 256, 320, 512, 1024, 1280, 1536, 64, 256, 1024]
+    models = [0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 1, 1]  # BC 1024 takes the global path
+    seeds = [wl.BASE_SEED + 600 + r for r in range(len(Ls))]
+    delta, n, k = 0.25, 24, 4
+    betas = np.linspace(0.35, 0.55, n)
+    ens = isg.Ensemble(Ls, seeds, models=models, delta=delta, record_capacity=8)
+    ens.init_random()
+    ens.sweep(10, betas=betas[:10], record_every=5)
+    ens.sweep(n - 10, betas=betas[10:], record_every=k)  # second call: graph update path
+    rows = ens.read_records()
+    assert len(rows) == 2 + (n - 10) // k
+    for r, (L, m, sd) in enumerate(zip(Ls, models, seeds)):
+        recs1, s = _alone(isg, L, m, sd, betas[:10], 5, delta)
+        lat = isg.Lattice(L, m, seed=sd, delta=delta, record_capacity=16)
+        lat.set(s, t=10)
+        lat.sweep(n - 10, betas=betas[10:], record_every=k)
+        recs = recs1 + lat.read_records()
+        final = lat.get()
+        lat.close()
+        assert len(recs) == len(rows)
+        for i, row in enumerate(rows):
+            _same_obs(row[r], recs[i])
+        assert np.array_equal(ens.get(r), final), (L, m)
+    # a few replicas straight against the oracle
+    for r in (0, 2, 9):
+        s = orc.init_random(Ls[r], models[r], seeds[r])
+        bmq, R, C = orc.run(s, models[r], seeds[r], 0, betas, delta=delta)
+        assert np.array_equal(ens.get(r), s)
+
+
+def test_ensemble_workload_subset_and_xi2(isg, orc):
+    """The replica-ensemble workload (uneven mix of L in {64..1024}, hot start
+    quenched to beta_c), 64 replicas covering all sizes, 300 sweeps recorded
+    every 100: bit-exact against lattices alone; the ensemble-mean xi_2 of the
+    L = 64 replicas equals the oracle's, computed from the oracle's own runs."""
+    Ls = wl.ensemble_sizes(64)
+    Ls[:5] = [64, 128, 256, 512, 1024]
+    seeds = [wl.BASE_SEED + 3 + r for r in range(64)]
+    n, k = 300, 100
+    ens = isg.Ensemble(Ls, seeds, record_capacity=4)
+    assert ens.autotune(2) in (256, 512, 1024)
+    ens.init_random()
+    ens.sweep(n, beta=wl.BETA_C_ISING, record_every=k)
+    rows = ens.read_records()
+    assert len(rows) == n // k
+    for r in range(0, 64, 7):
+        recs, s = _alone(isg, int(Ls[r]), 0, seeds[r], [wl.BETA_C_ISING] * n, k)
+        for i, row in enumerate(rows):
+            _same_obs(row[r], recs[i])
+        assert np.array_equal(ens.get(r), s)
+    idx = [r for r in range(64) if Ls[r] == 64]
+    assert len(idx) >= 3
+    M, R, C = [], [], []
+    for r in idx:
+        s = orc.init_random(64, 0, seeds[r])
+        bmq, Rr, Cr = orc.run(s, 0, seeds[r], 0, [wl.BETA_C_ISING] * n, record_every=k)
+        M.append(bmq[-1, 1])
+        R.append(Rr[-1])
+        C.append(Cr[-1])
+        assert np.array_equal(ens.get(r), s)
+    want = orc.xi2(M, np.array(R), np.array(C))
+    got = isg.xi2([rows[-1][r].M for r in idx], np.array([rows[-1][r].R for r in idx]),
+                  np.array([rows[-1][r].C for r in idx]))
+    assert (math.isnan(got) and math.isnan(want)) or abs(got - want) <= 1e-12 * abs(want)
+
+
+def test_ensemble_errors(isg):
+    with pytest.raises(isg.IsgError):
+        isg.Ensemble([100], [1])
+    ens = isg.Ensemble([64, 128], [1, 2], record_capacity=1)
+    ens.init_random()
+    with pytest.raises(isg.IsgError) as e:
+        ens.sweep(4, beta=0.4, record_every=2)  # two rows, room for one
+    assert e.value.status == -5
+    with pytest.raises(isg.IsgError):
+        ens.sweep(1, beta=-1.0)
