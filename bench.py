@@ -182,6 +182,47 @@ def batched_bench(sweeps=10000, n_rep=4096, record_every=1000):
             "ratio_vs_single": batched / single}
 
 
+def served_bench(n_req=48, load=0.9, chunk=100, max_active=48):
+    """The served stream: requests of the served workload (workloads.py)
+    through the continuous-batching server.  First all at once (capacity and
+    makespan), then with Poisson arrivals at `load` x that capacity (p50/p99
+    latency from arrival to completion, aggregate throughput)."""
+    import paper_2503_14688_b300 as P
+
+    reqs = wl.served_requests(n_req)
+    flips = [r["L"] ** 2 * r["sweeps"] for r in reqs]
+    total = float(sum(flips))
+    budget = 96 << 30
+
+    def run(arrivals):
+        srv = P.Server(hbm_budget=budget, max_active=max_active, chunk_sweeps=chunk)
+        ids = []
+        for r, a in zip(reqs, arrivals):
+            ids.append(srv.submit(r["model"], r["L"], r["seed"], r["sweeps"], r["t_start"],
+                                  r["beta"], arrival_time=a))
+        srv.drain()
+        res = [srv.poll(i) for i in ids]
+        srv.close()
+        lat = np.array([x.t_done - x.t_arrival for x in res])
+        t_first = min(x.t_arrival for x in res)
+        t_last = max(x.t_done for x in res)
+        return lat, t_last - t_first
+
+    lat0, span0 = run([0.0] * n_req)
+    capacity = total / span0  # flips/s with the queue always full
+    rate = load * capacity / (total / n_req)
+    arrivals = wl.poisson_arrivals(n_req, rate)
+    lat, span = run(list(arrivals))
+    return {"workload": f"{n_req} requests: Ising or Blume-Capel (p=1/2), L=2^k, k in 8..14, "
+                        f"sweeps log-uniform in [1e3, 1e4], 10-step bath 1.5 T_c -> 1.01 T_c; "
+                        f"chunk {chunk} sweeps, {max_active} slots",
+            "saturated": {"value": capacity / 1e9, "unit": UNIT, "makespan_s": span0},
+            "poisson": {"load": load, "rate_per_s": rate, "value": total / span / 1e9,
+                        "unit": UNIT, "p50_s": float(np.percentile(lat, 50)),
+                        "p99_s": float(np.percentile(lat, 99)), "makespan_s": span},
+            "total_flips": total}
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -325,6 +366,10 @@ def run_ours(args, w):
         }
         if not args.no_batched and world == 1:
             line["batched"] = batched_bench()
+            line["served"] = served_bench()
+            line["served"]["saturated"]["ratio_vs_single"] = (
+                line["served"]["saturated"]["value"] /
+                line["batched"]["single_lattice_equal_spins"]["value"])
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w.model, beta, w.delta)
         print(json.dumps(line), flush=True)

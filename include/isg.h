@@ -279,6 +279,81 @@ isg_status isg_ensemble_info(const isg_ensemble *ens, int64_t *n, int64_t *sweep
  * not changed).  *threads_out (may be NULL) = the choice.  Synchronises. */
 isg_status isg_ensemble_autotune(isg_ensemble *ens, int64_t sweeps, int32_t *threads_out);
 
+/* ---------------------------------------------------------------------------
+ * Request server with continuous batching.  Each request is one lattice
+ * (model, L, seed, Delta) run for n_sweeps sweeps under its own bath schedule
+ * beta(t) -- the direct quench (one piece) or the time-dependent bath of the
+ * pre-cooling protocol ("Thermal protocols"; Table II), or any stepped bath.
+ * The server works in rounds (isg_server_step): it retires finished
+ * requests, admits arrived requests in arrival order while the device-memory
+ * budget and the slot count allow, and advances every running request by
+ * chunk_sweeps sweeps -- lattices that fit in shared memory (Ising L <= 1280,
+ * Blume-Capel L <= 768) together in one persistent launch, larger ones on
+ * streams of their own, overlapping it.  A result does not depend on what
+ * else ran or where chunks were cut (per-site keying).
+ * ------------------------------------------------------------------------- */
+typedef struct isg_server isg_server;
+
+#define ISG_REQ_QUEUED 0
+#define ISG_REQ_RUNNING 1
+#define ISG_REQ_DONE 2
+
+typedef struct {
+    size_t hbm_budget;      /* device bytes requests may hold (capped at the free
+                               memory at creation)                               */
+    int32_t max_active;     /* requests resident at once (>= 1)                  */
+    int64_t chunk_sweeps;   /* sweeps per request per round (>= 1)               */
+    void *stream;           /* main stream; NULL = an internal stream            */
+} isg_server_desc;
+
+typedef struct {
+    int32_t model;
+    int64_t L;              /* a valid side and a multiple of 256                */
+    uint64_t seed;
+    double delta;           /* Blume-Capel crystal field                         */
+    int64_t n_sweeps;       /* >= 1                                              */
+    int64_t n_pieces;       /* beta(t) = beta[i] for t_start[i] <= t < t_start[i+1];
+                               t_start[0] = 0, increasing; copied at submit      */
+    const int64_t *t_start;
+    const double *beta;
+    int64_t record_every;   /* periodic records (0 = none); for requests batched
+                               in shared memory it must divide chunk_sweeps      */
+    int32_t keep_result;    /* 1: keep lattice and records until
+                               isg_server_release; 0: free them when done        */
+    double arrival_time;    /* seconds on the server clock; < 0 = now            */
+} isg_request;
+
+typedef struct {
+    int32_t state;          /* ISG_REQ_QUEUED / RUNNING / DONE                   */
+    int64_t sweeps_done;    /* n_sweeps once done                                */
+    int64_t B, M, Q;        /* final observables (state DONE)                    */
+    double t_arrival, t_admit, t_done;  /* server clock (s); t_done from a CUDA
+                               event after the request's last device work        */
+    int64_t records;        /* periodic records not yet read                     */
+} isg_result;
+
+isg_status isg_server_create(const isg_server_desc *desc, isg_server **out);
+void isg_server_destroy(isg_server *srv);  /* waits for the device; NULL accepted */
+/* Queue a request; *id identifies it.  ISG_ERR_OOM if it can never fit. */
+isg_status isg_server_submit(isg_server *srv, const isg_request *req, uint64_t *id);
+/* One scheduling round (asynchronous device work); counts after it. */
+isg_status isg_server_step(isg_server *srv, int32_t *active, int32_t *queued);
+/* Rounds until every submitted request is done (waits for arrivals). */
+isg_status isg_server_drain(isg_server *srv);
+isg_status isg_server_poll(isg_server *srv, uint64_t id, isg_result *out);
+/* Periodic records of a finished, kept request (as isg_read_records). */
+isg_status isg_server_read_records(isg_server *srv, uint64_t id, isg_obs *out, int64_t max,
+                                   int64_t *count);
+/* Final lattice of a finished, kept request (L*L host bytes).  Synchronises. */
+isg_status isg_server_get_lattice(isg_server *srv, uint64_t id, int8_t *out);
+/* Free the device memory of a finished request. */
+isg_status isg_server_release(isg_server *srv, uint64_t id);
+/* Seconds since creation (the clock of arrival and completion times). */
+double isg_server_clock(const isg_server *srv);
+/* Spin-flip attempts of finished requests; bytes held; budget. */
+isg_status isg_server_stats(const isg_server *srv, double *flips_done, size_t *bytes_in_use,
+                            size_t *budget);
+
 /* Energy per spin (-B + Delta Q) / L^2 of one record. */
 double isg_energy_density(const isg_obs *obs, int64_t L, double delta);
 

@@ -18,6 +18,7 @@ ISG_ERR_DEVICE_TIMEOUT = -4
 ISG_ERR_BUSY = -5
 ISG_ERR_UNSUPPORTED = -6
 ISG_NOALLOC_MAX_L = 1 << 18
+ISG_REQ_QUEUED, ISG_REQ_RUNNING, ISG_REQ_DONE = 0, 1, 2
 ISG_ISING = 0
 ISG_BLUME_CAPEL = 1
 
@@ -43,6 +44,26 @@ class isg_ensemble_desc(ctypes.Structure):
                 ("model", ctypes.POINTER(ctypes.c_int32)), ("seed", ctypes.POINTER(ctypes.c_uint64)),
                 ("delta", ctypes.c_double), ("stream", ctypes.c_void_p),
                 ("record_capacity", ctypes.c_int64)]
+
+
+class isg_server_desc(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int32),
+                ("chunk_sweeps", ctypes.c_int64), ("stream", ctypes.c_void_p)]
+
+
+class isg_request(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("L", ctypes.c_int64), ("seed", ctypes.c_uint64),
+                ("delta", ctypes.c_double), ("n_sweeps", ctypes.c_int64),
+                ("n_pieces", ctypes.c_int64), ("t_start", ctypes.POINTER(ctypes.c_int64)),
+                ("beta", ctypes.POINTER(ctypes.c_double)), ("record_every", ctypes.c_int64),
+                ("keep_result", ctypes.c_int32), ("arrival_time", ctypes.c_double)]
+
+
+class isg_result(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("sweeps_done", ctypes.c_int64),
+                ("B", ctypes.c_int64), ("M", ctypes.c_int64), ("Q", ctypes.c_int64),
+                ("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double),
+                ("t_done", ctypes.c_double), ("records", ctypes.c_int64)]
 
 
 class isg_schedule(ctypes.Structure):
@@ -88,6 +109,18 @@ PROTOTYPES = {
     "isg_ensemble_get": (_I32, [_P, _I64, _I8P]),
     "isg_ensemble_info": (_I32, [_P, _I64P, _I64P, _I64P, _I32P]),
     "isg_ensemble_autotune": (_I32, [_P, _I64, _I32P]),
+    "isg_server_create": (_I32, [ctypes.POINTER(isg_server_desc), ctypes.POINTER(_P)]),
+    "isg_server_destroy": (None, [_P]),
+    "isg_server_submit": (_I32, [_P, ctypes.POINTER(isg_request), _U64P]),
+    "isg_server_step": (_I32, [_P, _I32P, _I32P]),
+    "isg_server_drain": (_I32, [_P]),
+    "isg_server_poll": (_I32, [_P, _U64, ctypes.POINTER(isg_result)]),
+    "isg_server_read_records": (_I32, [_P, _U64, ctypes.POINTER(isg_obs), _I64, _I64P]),
+    "isg_server_get_lattice": (_I32, [_P, _U64, _I8P]),
+    "isg_server_release": (_I32, [_P, _U64]),
+    "isg_server_clock": (_F64, [_P]),
+    "isg_server_stats": (_I32, [_P, _F64P, ctypes.POINTER(ctypes.c_size_t),
+                                ctypes.POINTER(ctypes.c_size_t)]),
 }
 
 _lib = None

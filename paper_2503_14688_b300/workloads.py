@@ -92,3 +92,28 @@ def stepped_bath(T_c: float, n_sweeps: int, steps: int = 10, hi: float = 1.5, lo
     edges = [int(round(k * n_sweeps / steps)) for k in range(steps)]
     temps = [T_c * (hi + (lo - hi) * k / (steps - 1)) for k in range(steps)]
     return edges, [1.0 / T for T in temps]
+
+
+def served_requests(n: int, seed: int = BASE_SEED + 5, kmin: int = 8, kmax: int = 14,
+                    sweeps_lo: int = 1000, sweeps_hi: int = 10000):
+    """The served-stream workload: n requests, each Ising or Blume-Capel with
+    probability 1/2, L = 2^k with k uniform in [kmin, kmax], a sweep count
+    log-uniform in [sweeps_lo, sweeps_hi], seed BASE+5+i, and a bath stepping
+    in 10 equal pieces, linear in T, from 1.5 T_c down to 1.01 T_c."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        model = int(rng.integers(0, 2))
+        L = 1 << int(rng.integers(kmin, kmax + 1))
+        sweeps = int(round(math.exp(rng.uniform(math.log(sweeps_lo), math.log(sweeps_hi)))))
+        Tc = T_C_ISING if model == ISING else T_C_BLUME_CAPEL
+        t_start, beta = stepped_bath(Tc, sweeps, steps=10)
+        out.append({"model": model, "L": L, "sweeps": sweeps, "seed": seed + i,
+                    "t_start": t_start, "beta": beta})
+    return out
+
+
+def poisson_arrivals(n: int, rate_per_s: float, seed: int = BASE_SEED + 55) -> np.ndarray:
+    """Arrival times (s) of a Poisson process of the given rate."""
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate_per_s, size=n))
