@@ -31,7 +31,7 @@ namespace isg {
 namespace {
 
 constexpr int kSweepThreads = 128;
-constexpr int kSweepMinBlocks = 12;  // 40 registers: 48 warps per SM
+constexpr int kSweepMinBlocks = 10;  // 48 registers: 40 warps per SM
 constexpr int kMeasureThreads = 256;
 
 template <int V>
@@ -189,30 +189,42 @@ __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
     k_ising_half(uint32_t *__restrict__ tgt, const uint32_t *__restrict__ nbr, int64_t L,
                  int64_t W, int colour, int H, PhiloxLaunch pc, IsingThr thr)
 {
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
-    const int64_t y0 = (int64_t)blockIdx.y * H;
-    if (w0 >= W || y0 >= L)
+    // threads enumerate (row band, V-word group) pairs, groups fastest, so
+    // every block is full whatever the row width; rows and words fit 32 bits
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t tpr = (uint32_t)W / V;
+    const uint32_t band = g / tpr;
+    const uint32_t w0 = (g - band * tpr) * V;
+    const uint32_t Li = (uint32_t)L, Wi = (uint32_t)W;
+    const uint32_t y0 = band * (uint32_t)H;
+    if (y0 >= Li)
         return;
-    const int64_t y1 = y0 + H < L ? y0 + H : L;
-    const uint64_t qrow = (uint64_t)(L / 8);
+    const uint32_t y1 = y0 + H < Li ? y0 + H : Li;
+    const uint64_t qrow = (uint64_t)(Li / 8);
+    // edge words of the two parities (periodic in the row)
+    const uint32_t e_left = w0 == 0 ? Wi - 1 : w0 - 1;
+    const uint32_t e_right = w0 + V == Wi ? 0 : w0 + V;
 
-    Words<V> U = load_words<V>(nbr + (y0 == 0 ? L - 1 : y0 - 1) * W + w0);
-    Words<V> S = load_words<V>(nbr + y0 * W + w0);
-    for (int64_t y = y0; y < y1; ++y) {
-        const int64_t yd = y + 1 == L ? 0 : y + 1;
-        const Words<V> D = load_words<V>(nbr + yd * W + w0);
+    const uint32_t *nrow = nbr + (uint64_t)y0 * Wi;
+    uint32_t *trow = tgt + (uint64_t)y0 * Wi;
+    Words<V> U = load_words<V>(nbr + (uint64_t)(y0 == 0 ? Li - 1 : y0 - 1) * Wi + w0);
+    Words<V> S = load_words<V>(nrow + w0);
+    for (uint32_t y = y0; y < y1; ++y) {
+        const uint32_t *ndown = y + 1 == Li ? nbr : nrow + Wi;
+        const Words<V> D = load_words<V>(ndown + w0);
         const int parity = (colour ^ (int)y) & 1;
-        const uint32_t edge = __ldg(nbr + y * W + edge_word(w0, V, W, parity));
+        const uint32_t edge = __ldg(nrow + (parity == 0 ? e_left : e_right));
         const Words<V> X = side_words<V>(S, edge, parity);
-        Words<V> T = load_words_rw<V>(tgt + y * W + w0);
+        Words<V> T = load_words_rw<V>(trow + w0);
+        const uint64_t qy = (uint64_t)y * qrow + 8u * w0;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)(w0 + v);
-            T.v[v] = ising_word_update(T.v[v], U.v[v], D.v[v], S.v[v], X.v[v], q0, pc, thr);
-        }
-        store_words<V>(tgt + y * W + w0, T);
+        for (int v = 0; v < V; ++v)
+            T.v[v] = ising_word_update(T.v[v], U.v[v], D.v[v], S.v[v], X.v[v], qy + 8u * v, pc, thr);
+        store_words<V>(trow + w0, T);
         U = S;
         S = D;
+        nrow += Wi;
+        trow += Wi;
     }
 }
 
@@ -234,9 +246,12 @@ __global__ void __launch_bounds__(kSweepThreads)
         s_thr[i] = tab.thr[i];
     __syncthreads();
 
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * V;
-    const int64_t y0 = (int64_t)blockIdx.y * H;
-    if (w0 >= W || y0 >= L)
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tpr = W / V;
+    const int64_t band = g / tpr;
+    const int64_t w0 = (g - band * tpr) * V;
+    const int64_t y0 = band * H;
+    if (y0 >= L)
         return;
     const int64_t y1 = y0 + H < L ? y0 + H : L;
     const uint64_t qrow = (uint64_t)(L / 8);
@@ -566,18 +581,20 @@ __global__ void k_unpack_rect(Planes pl, int64_t y0, int64_t x0, int64_t h, int6
 }
 
 // Rows per thread for a sweep launch: at most 64, fewer while the grid would
-// give less than about eight waves of resident blocks (tail balance), more
-// if the number of row bands would exceed the grid's y limit.
+// give less than about eight waves of resident blocks (tail balance).
 int sweep_band(int64_t L, int64_t threads_per_row)
 {
-    const int64_t bx = (threads_per_row + kSweepThreads - 1) / kSweepThreads;
-    const int64_t want_blocks = 148LL * kSweepMinBlocks * 8;
+    const int64_t want_threads = 148LL * kSweepMinBlocks * 8 * kSweepThreads;
     int H = 64;
-    while (H > 1 && bx * (L / H) < want_blocks)
+    while (H > 1 && threads_per_row * ((L + H - 1) / H) < want_threads)
         H >>= 1;
-    while ((L + H - 1) / H > 65535)
-        H <<= 1;
     return H;
+}
+
+unsigned sweep_blocks(int64_t L, int64_t threads_per_row, int H)
+{
+    const int64_t threads = threads_per_row * ((L + H - 1) / H);
+    return (unsigned)((threads + kSweepThreads - 1) / kSweepThreads);
 }
 
 template <int V>
@@ -589,9 +606,7 @@ cudaError_t launch_ising(const Planes &pl, int colour, const PhiloxLaunch &ph, c
     const uint32_t *nbr = pl.base + (int64_t)(1 - colour) * LW;
     const int64_t tpr = pl.W / V;
     const int H = sweep_band(pl.L, tpr);
-    const dim3 grid((unsigned)((tpr + kSweepThreads - 1) / kSweepThreads),
-                    (unsigned)((pl.L + H - 1) / H));
-    k_ising_half<V><<<grid, kSweepThreads, 0, st>>>(tgt, nbr, pl.L, pl.W, colour, H, ph, thr);
+    k_ising_half<V><<<sweep_blocks(pl.L, tpr, H), kSweepThreads, 0, st>>>(tgt, nbr, pl.L, pl.W, colour, H, ph, thr);
     return cudaGetLastError();
 }
 
@@ -606,9 +621,7 @@ cudaError_t launch_bc(const Planes &pl, int colour, const PhiloxLaunch &ph, cons
     const uint32_t *np = nn + LW;
     const int64_t tpr = pl.W / V;
     const int H = sweep_band(pl.L, tpr);
-    const dim3 grid((unsigned)((tpr + kSweepThreads - 1) / kSweepThreads),
-                    (unsigned)((pl.L + H - 1) / H));
-    k_bc_half<V><<<grid, kSweepThreads, 0, st>>>(tn, tp, nn, np, pl.L, pl.W, colour, H, ph, tab);
+    k_bc_half<V><<<sweep_blocks(pl.L, tpr, H), kSweepThreads, 0, st>>>(tn, tp, nn, np, pl.L, pl.W, colour, H, ph, tab);
     return cudaGetLastError();
 }
 
