@@ -66,7 +66,8 @@ struct EnsArgs {
 size_t smem_bytes_for(int32_t model, int64_t L)
 {
     const size_t planes = (size_t)L * (size_t)L / (model == ISG_ISING ? 8 : 4);
-    return planes + 8 * (size_t)L + 4 * kBcTableSize + 64;
+    const size_t spread = model == ISG_ISING ? 0 : sizeof(uint2) * kBcSpread * 256;
+    return planes + 8 * (size_t)L + 4 * kBcTableSize + 64 + spread;
 }
 
 // ---------------------------------------------------------------------------
@@ -214,11 +215,14 @@ __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
     int32_t *C_s = R_s + L;
     uint32_t *s_thr = reinterpret_cast<uint32_t *>(C_s + L);
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(s_thr + kBcTableSize);
+    uint2 *s_spread = reinterpret_cast<uint2 *>(acc + 4);  // Blume-Capel only
 
     const uint4 *g4 = reinterpret_cast<const uint4 *>(it.planes);
     uint4 *s4 = reinterpret_cast<uint4 *>(P);
     for (int i = tid; i < nplanes * LW / 4; i += nt)
         s4[i] = g4[i];
+    if (MODEL == 1)
+        bc_spread_fill(s_spread, tid, nt);
     __syncthreads();
 
     const int dy = nt / W, dw = nt - (nt / W) * W;
@@ -276,7 +280,7 @@ __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
                                             side_word(sp, nbp[y * W + ew], par)};
                     uint32_t n = tn[y * W + w], p = tp[y * W + w];
                     const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)w;
-                    bc_word_update(n, p, nn, pp, q0, pc, s_thr);
+                    bc_word_update(n, p, nn, pp, q0, pc, s_thr, s_spread);
                     tn[y * W + w] = n;
                     tp[y * W + w] = p;
                     w += dw;

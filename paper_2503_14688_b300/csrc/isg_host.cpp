@@ -74,7 +74,7 @@ void bc_table(double beta, double delta, BcTable *out)
                 uint32_t thr = always;
                 if (dE > 0.0)
                     thr = (uint32_t)grid_threshold(beta, dE, 31);
-                out->thr[(n << 6) | (p << 5) | (b << 4) | g] = thr;
+                out->thr[(b << 6) | (n << 5) | (p << 4) | g] = thr;
             }
         }
     }

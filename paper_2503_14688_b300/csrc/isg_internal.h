@@ -35,8 +35,8 @@ struct IsingThr {
     uint32_t full4, full8;
 };
 
-// Blume-Capel acceptance table: entry (n << 6) | (p << 5) | (b << 4) | g
-// for the current value s (n = s != 0, p = s > 0), the proposal bit b and
+// Blume-Capel acceptance table: entry (b << 6) | (n << 5) | (p << 4) | g for
+// the current value s (n = s != 0, p = s > 0), the proposal bit b and
 // g = h + 4 in [0, 8] (h = neighbour sum).  Accept iff (u >> 1) < entry;
 // entry = 2^31 means always.
 constexpr int kBcTableSize = 128;

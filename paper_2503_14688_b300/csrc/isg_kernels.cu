@@ -32,6 +32,7 @@ namespace {
 
 constexpr int kSweepThreads = 128;
 constexpr int kSweepMinBlocks = 10;  // 48 registers: 40 warps per SM
+constexpr int kBcMinBlocks = 6;      // 80 registers: 24 warps per SM
 constexpr int kMeasureThreads = 256;
 
 template <int V>
@@ -236,14 +237,16 @@ __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
 // (n, p, proposal bit, h + 4) held in shared memory.
 // ---------------------------------------------------------------------------
 template <int V>
-__global__ void __launch_bounds__(kSweepThreads)
+__global__ void __launch_bounds__(kSweepThreads, kBcMinBlocks)
     k_bc_half(uint32_t *__restrict__ tn_plane, uint32_t *__restrict__ tp_plane,
               const uint32_t *__restrict__ nn_plane, const uint32_t *__restrict__ np_plane,
               int64_t L, int64_t W, int colour, int H, PhiloxLaunch pc, BcTable tab)
 {
     __shared__ uint32_t s_thr[kBcTableSize];
+    __shared__ uint2 s_spread[kBcSpread * 256];
     for (int i = threadIdx.x; i < kBcTableSize; i += blockDim.x)
         s_thr[i] = tab.thr[i];
+    bc_spread_fill(s_spread, threadIdx.x, blockDim.x);
     __syncthreads();
 
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -276,7 +279,7 @@ __global__ void __launch_bounds__(kSweepThreads)
             const uint32_t nbn[4] = {Un.v[v], Dn.v[v], Sn.v[v], Xn.v[v]};
             const uint32_t nbp[4] = {Up.v[v], Dp.v[v], Sp.v[v], Xp.v[v]};
             const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)(w0 + v);
-            bc_word_update(Tn.v[v], Tp.v[v], nbn, nbp, q0, pc, s_thr);
+            bc_word_update(Tn.v[v], Tp.v[v], nbn, nbp, q0, pc, s_thr, s_spread);
         }
         store_words<V>(tn_plane + y * W + w0, Tn);
         store_words<V>(tp_plane + y * W + w0, Tp);

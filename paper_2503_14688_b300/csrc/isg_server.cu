@@ -66,12 +66,6 @@ isg_status scuda(cudaError_t e, const char *what)
 
 constexpr int kSmemLimit = kBatchSmemMax;
 
-size_t batch_smem_bytes(int32_t model, int64_t L)
-{
-    const size_t planes = (size_t)L * (size_t)L / (model == ISG_ISING ? 8 : 4);
-    return planes + 8 * (size_t)L + 4 * kBcTableSize + 64;
-}
-
 struct Request {
     uint64_t id = 0;
     int32_t model = 0;
@@ -524,7 +518,7 @@ isg_status isg_server_submit(isg_server *s, const isg_request *q, uint64_t *id)
     r->record_every = q->record_every;
     r->keep = q->keep_result;
     r->t_arrival = q->arrival_time >= 0 ? q->arrival_time : clock_now(s);
-    r->small = batch_smem_bytes(r->model, r->L) <= (size_t)kSmemLimit;
+    r->small = smem_bytes_for(r->model, r->L) <= (size_t)kSmemLimit;
     r->rec_cap = q->record_every > 0 ? q->n_sweeps / q->record_every : 0;
     // batched requests record inside the kernel at multiples of record_every
     // counted from each chunk's start: keep chunks aligned to record_every

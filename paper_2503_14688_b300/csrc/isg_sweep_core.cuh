@@ -98,15 +98,41 @@ __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uin
     cy = (a & b) | (c & (a ^ b));
 }
 
+// Blume-Capel per-site threshold lookup.  The table index of a site is
+// (b << 6) | (n << 5) | (p << 4) | g with b its proposal bit (u & 1), n, p its
+// bit-planes and g = h + 4; as a byte offset into the 128-entry u32 table:
+// (b << 8) | (idx6 << 2), idx6 = (n << 5) | (p << 4) | g.
+//
+// The six planes g0..g3, p, n are known before the random numbers; their
+// bits are spread to one byte per site with 256-entry lookup tables in
+// shared memory: kBcSpread tables (one per plane k), entry v holding, in
+// byte m of a 64-bit word, bit k + 2 equal to bit m of v.  OR-ing the six
+// entries of a byte of each plane gives the scaled index of 8 sites at once.
+constexpr int kBcSpread = 6;
+
+__device__ __forceinline__ void bc_spread_fill(uint2 *s_spread, int tid, int nt)
+{
+    for (int i = tid; i < kBcSpread * 256; i += nt) {
+        const int k = i >> 8, v = i & 255;
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            lo |= (uint32_t)((v >> m) & 1) << (8 * m + k + 2);
+            hi |= (uint32_t)((v >> (m + 4)) & 1) << (8 * m + k + 2);
+        }
+        s_spread[i] = make_uint2(lo, hi);
+    }
+}
+
 // Blume-Capel: new (n, p) target words.  Neighbour planes nbn/nbp hold the
 // up, down, same and side words.  The field h + 4 = #(+1 neighbours) +
-// #(neighbours != -1) is summed bit-sliced into g0..g3; each site looks its
-// threshold up in the 128-entry table s_thr (index (n, p, b, h + 4)) and
-// accepts iff (u >> 1) < entry.  Proposal: p' = b & ~(n & p),
+// #(neighbours != -1) is summed bit-sliced into g0..g3; each site accepts iff
+// (u >> 1) < its table entry (2^31 = always).  Proposal: p' = b & ~(n & p),
 // n' = ~n | (p ^ b) with b = u & 1.
 __device__ __forceinline__ void bc_word_update(uint32_t &n, uint32_t &p, const uint32_t (&nbn)[4],
                                                const uint32_t (&nbp)[4], uint64_t q0,
-                                               const PhiloxLaunch &pc, const uint32_t *s_thr)
+                                               const PhiloxLaunch &pc, const uint32_t *s_thr,
+                                               const uint2 *s_spread)
 {
     // eight indicators: s_i = +1 (n & p), s_i != -1 (~n | p)
     const uint32_t x0 = nbn[0] & nbp[0], x1 = ~nbn[0] | nbp[0];
@@ -122,24 +148,41 @@ __device__ __forceinline__ void bc_word_update(uint32_t &n, uint32_t &p, const u
     const uint32_t g1 = se ^ cd, cf = se & cd;
     const uint32_t g2 = ce ^ cf;  // weight-4 column
     const uint32_t g3 = ce & cf;  // only when h + 4 = 8
+    const uint32_t planes[kBcSpread] = {g0, g1, g2, g3, p, n};
 
+    const char *thr_bytes = reinterpret_cast<const char *>(s_thr);
     const PhiloxWordPart wp = philox_word_part(pc, (uint32_t)(q0 >> 32));
-    uint32_t acc = 0, bits = 0;
+    uint32_t rej = 0, bits = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        uint32_t r[4];
-        philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
+    for (int j = 0; j < 4; ++j) {
+        // scaled table index of sites 8j .. 8j+7, one byte each
+        uint32_t lo = 0, hi = 0;
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int bi = 4 * i + k;
-            const uint32_t bb = r[k] & 1u;
-            const uint32_t idx = (((n >> bi) & 1u) << 6) | (((p >> bi) & 1u) << 5) | (bb << 4) |
-                                 (((g3 >> bi) & 1u) << 3) | (((g2 >> bi) & 1u) << 2) |
-                                 (((g1 >> bi) & 1u) << 1) | ((g0 >> bi) & 1u);
-            acc |= (uint32_t)((r[k] >> 1) < s_thr[idx]) << bi;
-            bits |= bb << bi;
+        for (int k = 0; k < kBcSpread; ++k) {
+            const uint2 e = s_spread[k * 256 + ((planes[k] >> (8 * j)) & 0xFFu)];
+            lo |= e.x;
+            hi |= e.y;
+        }
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            uint32_t r[4];
+            philox_site4(pc, wp, (uint32_t)q0 + 2 * j + i, r[0], r[1], r[2], r[3]);
+            const uint32_t word = i ? hi : lo;
+            uint32_t nr = 0, nb = 0;
+#pragma unroll
+            for (int kk = 3; kk >= 0; --kk) {
+                // byte kk of word (the site's index) and bit 0 of u (b) at bit 8
+                const uint32_t off = __byte_perm(word, r[kk], 0x0040u | (uint32_t)kk) & 0x1FCu;
+                const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
+                nr = shift_in_not_below(nr, r[kk] >> 1, thr);
+                nb = (nb << 1) | (r[kk] & 1u);
+            }
+            const int sh = 8 * j + 4 * i;
+            rej = nr * (1u << sh) + rej;
+            bits = nb * (1u << sh) + bits;
         }
     }
+    const uint32_t acc = ~rej;
     const uint32_t np2 = bits & ~(n & p);
     const uint32_t nn2 = ~n | (p ^ bits);
     const uint32_t n_old = n, p_old = p;
