@@ -208,6 +208,26 @@ def served_bench(n_req=48, load=0.9, chunk=100, max_active=48):
         t_last = max(x.t_done for x in res)
         return lat, t_last - t_first
 
+    # single-lattice reference at equal spins: each model's rate on one
+    # L = 32768 lattice, combined with the mix's flips of that model
+    import torch
+
+    ref_rate = {}
+    for model in (wl.ISING, wl.BLUME_CAPEL):
+        lat = P.Lattice(32768, model, seed=wl.BASE_SEED + 5)
+        lat.init_random()
+        beta = wl.BETA_C_ISING if model == wl.ISING else 1.0 / wl.T_C_BLUME_CAPEL
+        lat.sweep(2, beta=beta)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lat.sweep(50, beta=beta)
+        b.record()
+        torch.cuda.synchronize()
+        ref_rate[model] = 32768.0 ** 2 * 50 / (a.elapsed_time(b) * 1e-3)
+        lat.close()
+    ref = total / sum(f / ref_rate[r["model"]] for f, r in zip(flips, reqs))
+
     lat0, span0 = run([0.0] * n_req)
     capacity = total / span0  # flips/s with the queue always full
     rate = load * capacity / (total / n_req)
@@ -216,7 +236,12 @@ def served_bench(n_req=48, load=0.9, chunk=100, max_active=48):
     return {"workload": f"{n_req} requests: Ising or Blume-Capel (p=1/2), L=2^k, k in 8..14, "
                         f"sweeps log-uniform in [1e3, 1e4], 10-step bath 1.5 T_c -> 1.01 T_c; "
                         f"chunk {chunk} sweeps, {max_active} slots",
-            "saturated": {"value": capacity / 1e9, "unit": UNIT, "makespan_s": span0},
+            "saturated": {"value": capacity / 1e9, "unit": UNIT, "makespan_s": span0,
+                          "single_lattice_mix": {"value": ref / 1e9, "unit": UNIT,
+                                                 "ising_L32768": ref_rate[wl.ISING] / 1e9,
+                                                 "blume_capel_L32768":
+                                                     ref_rate[wl.BLUME_CAPEL] / 1e9},
+                          "ratio_vs_single": capacity / ref},
             "poisson": {"load": load, "rate_per_s": rate, "value": total / span / 1e9,
                         "unit": UNIT, "p50_s": float(np.percentile(lat, 50)),
                         "p99_s": float(np.percentile(lat, 99)), "makespan_s": span},
@@ -365,11 +390,8 @@ def run_ours(args, w):
             "xi2_last": xi,
         }
         if not args.no_batched and world == 1:
-            line["batched"] = batched_bench()
-            line["served"] = served_bench()
-            line["served"]["saturated"]["ratio_vs_single"] = (
-                line["served"]["saturated"]["value"] /
-                line["batched"]["single_lattice_equal_spins"]["value"])
+            line["batched"] = batched_bench(sweeps=args.batched_sweeps, n_rep=args.batched_replicas)
+            line["served"] = served_bench(n_req=args.served_requests)
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w.model, beta, w.delta)
         print(json.dumps(line), flush=True)
@@ -389,9 +411,21 @@ def main():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the replica-ensemble measurement")
     ap.add_argument("--L", type=int, default=0, help="override the workload's L (profiling)")
+    ap.add_argument("--batched-replicas", type=int, default=4096)
+    ap.add_argument("--batched-sweeps", type=int, default=10000)
+    ap.add_argument("--served-requests", type=int, default=48)
+    ap.add_argument("--only-batched", action="store_true",
+                    help="print only the replica-ensemble measurement (profiling)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.only_batched:
+        import torch
+
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        print(json.dumps(batched_bench(sweeps=args.batched_sweeps, n_rep=args.batched_replicas,
+                                       record_every=max(1, args.batched_sweeps // 10))), flush=True)
+        return
     w = _workload(args.workload)
     if args.L:
         w.L = args.L
