@@ -32,7 +32,8 @@ namespace {
 
 constexpr int kSweepThreads = 128;
 constexpr int kSweepMinBlocks = 10;  // 48 registers: 40 warps per SM
-constexpr int kBcMinBlocks = 6;      // 80 registers: 24 warps per SM
+constexpr int kBcThreads = 256;
+constexpr int kBcMinBlocks = 3;      // 85 registers: 24 warps per SM
 constexpr int kMeasureThreads = 256;
 
 template <int V>
@@ -237,7 +238,7 @@ __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
 // (n, p, proposal bit, h + 4) held in shared memory.
 // ---------------------------------------------------------------------------
 template <int V>
-__global__ void __launch_bounds__(kSweepThreads, kBcMinBlocks)
+__global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
     k_bc_half(uint32_t *__restrict__ tn_plane, uint32_t *__restrict__ tp_plane,
               const uint32_t *__restrict__ nn_plane, const uint32_t *__restrict__ np_plane,
               int64_t L, int64_t W, int colour, int H, PhiloxLaunch pc, BcTable tab)
@@ -624,7 +625,9 @@ cudaError_t launch_bc(const Planes &pl, int colour, const PhiloxLaunch &ph, cons
     const uint32_t *np = nn + LW;
     const int64_t tpr = pl.W / V;
     const int H = sweep_band(pl.L, tpr);
-    k_bc_half<V><<<sweep_blocks(pl.L, tpr, H), kSweepThreads, 0, st>>>(tn, tp, nn, np, pl.L, pl.W, colour, H, ph, tab);
+    const int64_t threads = tpr * ((pl.L + H - 1) / H);
+    k_bc_half<V><<<(unsigned)((threads + kBcThreads - 1) / kBcThreads), kBcThreads, 0, st>>>(
+        tn, tp, nn, np, pl.L, pl.W, colour, H, ph, tab);
     return cudaGetLastError();
 }
 
