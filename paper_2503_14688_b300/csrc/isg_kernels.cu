@@ -410,25 +410,33 @@ __global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
             Sn = __ldg(n0 + y0 * W + wc);
         }
     }
+    // Bands start at multiples of 16 rows and groups at multiples of 4, so row
+    // yg + r has parity r & 1 (known at compile time) and the only periodic
+    // wrap is the down neighbour of row L - 1.  Column pointers; the edge word
+    // of the colour-1 site is to the left on odd rows, to the right on even.
+    const uint32_t *p0c = p0 + wc, *p1c = p1 + wc;
+    const uint32_t *n0c = n0 + wc, *n1c = n1 + wc;
+    const int64_t off_l = wl - wc, off_r = wr - wc;
     for (int r0 = 0; r0 < rows; r0 += 16) {
 #pragma unroll 1
         for (int g = 0; g < 4; ++g) {
             const int64_t yg = y0 + r0 + 4 * g;
+            const bool last = yg + 4 == L;  // row yg + 3 wraps to row 0
             uint32_t Tp[4], Dp[4], Ep[4], Tn[4], Dn[4], En[4];
             if (active) {
+                const uint32_t *t1 = p1c + yg * W, *t0 = p0c + yg * W;
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
-                    const int64_t y = yg + r;
-                    const int64_t yd = y + 1 == L ? 0 : y + 1;
-                    // colour-1 parity (1 ^ y) & 1: 0 -> left neighbour word, 1 -> right
-                    const int64_t ew = y * W + ((y & 1) ? wl : wr);
-                    Tp[r] = __ldg(p1 + y * W + wc);
-                    Dp[r] = __ldg(p0 + yd * W + wc);
-                    Ep[r] = __ldg(p0 + ew);
+                    const uint32_t *down = (r == 3 && last) ? p0c : t0 + (r + 1) * W;
+                    const uint32_t *edge = t0 + r * W + ((r & 1) ? off_l : off_r);
+                    Tp[r] = __ldg(t1 + r * W);
+                    Dp[r] = __ldg(down);
+                    Ep[r] = __ldg(edge);
                     if (MODEL == 1) {
-                        Tn[r] = __ldg(n1 + y * W + wc);
-                        Dn[r] = __ldg(n0 + yd * W + wc);
-                        En[r] = __ldg(n0 + ew);
+                        const int64_t d_nb = n0c - p0c;  // occupancy planes: fixed offset
+                        Tn[r] = __ldg(t1 + r * W + (n1c - p1c));
+                        Dn[r] = __ldg(down + d_nb);
+                        En[r] = __ldg(edge + d_nb);
                     }
                 }
             } else {
@@ -439,7 +447,7 @@ __global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
             uint32_t evp[4], odp[4], evm[4], odm[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const bool odd = (yg + r) & 1;
+                const bool odd = r & 1;
                 const uint32_t Xp = odd ? (Sp << 1) | (Ep[r] >> 31) : (Sp >> 1) | (Ep[r] << 31);
                 int rowpart;
                 if (MODEL == 0) {
