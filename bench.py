@@ -295,8 +295,10 @@ def run_ours(args, w):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2503_14688_b300 as P
 
+    from paper_2503_14688_b300 import replicas
+
     stream = torch.cuda.Stream()
-    seed = w.seed + rank  # replicas: independent lattices, one per rank
+    seed = replicas.replica_seed(w.seed, rank)  # replicas: independent lattices, one per rank
     lat = P.Lattice(w.L, w.model, seed=seed, delta=w.delta, stream=stream,
                     record_capacity=args.steps + args.warmup + 4)
     lat.init_random()
@@ -349,13 +351,10 @@ def run_ours(args, w):
         P.xi2([r.M], r.R[None], r.C[None])
     e2e_s = time.perf_counter() - t0
 
-    ms_t = torch.tensor([ms, e2e_s], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms, e2e_s = float(ms_t[0]), float(ms_t[1])
+    ms, e2e_s = replicas.max_over_ranks([ms, e2e_s], device="cuda")
     sites = float(w.L) * float(w.L)
-    value = world * sites * args.steps / (ms * 1e6)
-    e2e_value = world * sites * e2e_steps / (e2e_s * 1e9)
+    value = replicas.weak_scaling_value(world, sites, args.steps, ms)
+    e2e_value = replicas.weak_scaling_value(world, sites, e2e_steps, e2e_s * 1e3)
 
     sm_max, peak_src = _peaks()
     peak = SMS * INT_LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s

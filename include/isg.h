@@ -139,6 +139,21 @@ isg_status isg_lattice_get_rect(isg_lattice *lat, int64_t y0, int64_t x0, int64_
 /* Whole lattice (L*L host bytes); the same as the rect with the full size. */
 isg_status isg_lattice_get(isg_lattice *lat, int8_t *out);
 
+/* Checkpoint: write the lattice to `path` -- a 64-byte header (magic
+ * "ISGLAT01", int32 model, int32 0, int64 L, uint64 seed, double delta,
+ * int64 sweep counter, uint64 plane bytes, 8 bytes 0), then the spin planes
+ * exactly as stored on the device (little-endian 32-bit words).  Pending
+ * records are not saved.  Synchronises; streams through a 64 MiB pinned
+ * buffer, so lattices larger than host memory can be saved. */
+isg_status isg_save(isg_lattice *lat, const char *path);
+
+/* Resume: create a lattice (on the current device, work on `stream`, with
+ * `record_capacity` record slots) from a file written by isg_save.  Sweeping
+ * it continues the run bit for bit (the random numbers depend only on seed,
+ * sweep index, colour and site).  ISG_ERR_INVALID for a missing, short or
+ * foreign file.  Synchronises. */
+isg_status isg_load(const char *path, void *stream, int64_t record_capacity, isg_lattice **out);
+
 /* Sweep counter (sweeps done so far), L, model, seed. */
 isg_status isg_lattice_info(const isg_lattice *lat, int64_t *sweep, int64_t *L,
                             int32_t *model, uint64_t *seed);

@@ -90,6 +90,8 @@ PROTOTYPES = {
     "isg_lattice_get_rect": (_I32, [_P, _I64, _I64, _I64, _I64, _I8P]),
     "isg_lattice_get": (_I32, [_P, _I8P]),
     "isg_lattice_info": (_I32, [_P, _I64P, _I64P, _I32P, _U64P]),
+    "isg_save": (_I32, [_P, ctypes.c_char_p]),
+    "isg_load": (_I32, [ctypes.c_char_p, _P, _I64, ctypes.POINTER(_P)]),
     "isg_sweep": (_I32, [_P, _I64, _F64P, _F64, _I64]),
     "isg_sweep_schedule": (_I32, [_P, _I64, ctypes.POINTER(isg_schedule), _I64]),
     "isg_half_sweep": (_I32, [_P, _I32, _F64]),

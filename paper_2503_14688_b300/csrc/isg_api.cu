@@ -3,6 +3,7 @@
 // schedules), the on-device record ring and the host-side reads.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -470,6 +471,117 @@ isg_status isg_measure(isg_lattice *lat, isg_obs *out)
         return s;
     ISG_CUDA(cudaStreamSynchronize(lat->stream), "stream sync");
     return copy_record(lat, slot, out);
+}
+
+namespace {
+
+struct FileHeader {
+    char magic[8];
+    int32_t model;
+    int32_t zero;
+    int64_t L;
+    uint64_t seed;
+    double delta;
+    int64_t sweep;
+    uint64_t plane_bytes;
+    uint64_t pad;
+};
+static_assert(sizeof(FileHeader) == 64, "checkpoint header is 64 bytes");
+const char kMagic[8] = {'I', 'S', 'G', 'L', 'A', 'T', '0', '1'};
+constexpr size_t kChunk = (size_t)64 << 20;
+
+}  // namespace
+
+isg_status isg_save(isg_lattice *lat, const char *path)
+{
+    if (!lat || !path)
+        return fail(ISG_ERR_INVALID, "lattice and path must not be NULL");
+    FileHeader h{};
+    memcpy(h.magic, kMagic, 8);
+    h.model = lat->model;
+    h.L = lat->L;
+    h.seed = lat->seed;
+    h.delta = lat->delta;
+    h.sweep = lat->t;
+    h.plane_bytes = isg_lattice_bytes(lat->model, lat->L);
+    ISG_CUDA(cudaStreamSynchronize(lat->stream), "stream sync");
+    FILE *f = fopen(path, "wb");
+    if (!f)
+        return fail(ISG_ERR_INVALID, "cannot open %s for writing", path);
+    void *bounce = nullptr;
+    cudaError_t e = cudaMallocHost(&bounce, kChunk);
+    bool ok = e == cudaSuccess && fwrite(&h, sizeof(h), 1, f) == 1;
+    const uint8_t *src = reinterpret_cast<const uint8_t *>(lat->planes);
+    for (uint64_t done = 0; ok && done < h.plane_bytes;) {
+        const size_t n = (size_t)std::min<uint64_t>(kChunk, h.plane_bytes - done);
+        e = cudaMemcpy(bounce, src + done, n, cudaMemcpyDeviceToHost);
+        ok = e == cudaSuccess && fwrite(bounce, 1, n, f) == n;
+        done += n;
+    }
+    if (bounce)
+        cudaFreeHost(bounce);
+    ok = (fclose(f) == 0) && ok;
+    if (e != cudaSuccess)
+        return cuda_fail(e, "checkpoint copy");
+    if (!ok)
+        return fail(ISG_ERR_INVALID, "write to %s failed", path);
+    return ISG_OK;
+}
+
+isg_status isg_load(const char *path, void *stream, int64_t record_capacity, isg_lattice **out)
+{
+    if (out)
+        *out = nullptr;
+    if (!path || !out)
+        return fail(ISG_ERR_INVALID, "path and out must not be NULL");
+    FILE *f = fopen(path, "rb");
+    if (!f)
+        return fail(ISG_ERR_INVALID, "cannot open %s", path);
+    FileHeader h{};
+    if (fread(&h, sizeof(h), 1, f) != 1 || memcmp(h.magic, kMagic, 8) != 0 ||
+        !valid_L(h.model, h.L) || h.plane_bytes != isg_lattice_bytes(h.model, h.L) ||
+        h.sweep < 0 || h.sweep > (int64_t)0xFFFFFFFFLL) {
+        fclose(f);
+        return fail(ISG_ERR_INVALID, "%s is not a lattice checkpoint", path);
+    }
+    isg_lattice_desc d{};
+    d.model = h.model;
+    d.L = h.L;
+    d.seed = h.seed;
+    d.delta = h.delta;
+    d.stream = stream;
+    d.record_capacity = record_capacity;
+    isg_lattice *lat = nullptr;
+    isg_status st = isg_lattice_create(&d, &lat);
+    if (st != ISG_OK) {
+        fclose(f);
+        return st;
+    }
+    void *bounce = nullptr;
+    cudaError_t e = cudaMallocHost(&bounce, kChunk);
+    bool ok = e == cudaSuccess;
+    uint8_t *dst = reinterpret_cast<uint8_t *>(lat->planes);
+    for (uint64_t done = 0; ok && done < h.plane_bytes;) {
+        const size_t n = (size_t)std::min<uint64_t>(kChunk, h.plane_bytes - done);
+        ok = fread(bounce, 1, n, f) == n;
+        if (ok) {
+            e = cudaMemcpy(dst + done, bounce, n, cudaMemcpyHostToDevice);
+            ok = e == cudaSuccess;
+        }
+        done += n;
+    }
+    if (bounce)
+        cudaFreeHost(bounce);
+    fclose(f);
+    if (!ok) {
+        isg_lattice_destroy(lat);
+        if (e != cudaSuccess)
+            return cuda_fail(e, "checkpoint copy");
+        return fail(ISG_ERR_INVALID, "%s is truncated", path);
+    }
+    lat->t = h.sweep;
+    *out = lat;
+    return ISG_OK;
 }
 
 double isg_xi2(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const int32_t *C)

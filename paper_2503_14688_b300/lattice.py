@@ -103,6 +103,25 @@ class Lattice:
                                              out.ctypes.data_as(_abi._I8P)))
         return out
 
+    def save(self, path: str):
+        """Checkpoint to a file (isg_save)."""
+        check(self._lib.isg_save(self._h, str(path).encode()))
+
+    @classmethod
+    def load(cls, path: str, stream=None, record_capacity: int = 16) -> "Lattice":
+        """Resume from a checkpoint file (isg_load)."""
+        self = cls.__new__(cls)
+        self._lib = lib()
+        self._buf = None
+        self._h = ctypes.c_void_p()
+        check(self._lib.isg_load(str(path).encode(), _stream_handle(stream), int(record_capacity),
+                                 ctypes.byref(self._h)))
+        L, model = ctypes.c_int64(), ctypes.c_int32()
+        check(self._lib.isg_lattice_info(self._h, None, ctypes.byref(L), ctypes.byref(model), None))
+        self.L, self.model = L.value, model.value
+        self.delta = 0.0
+        return self
+
     @property
     def sweep_index(self) -> int:
         t = ctypes.c_int64()

@@ -91,3 +91,15 @@ def test_xi2_host_arithmetic_matches_oracle_bitwise(abi, orc):
             M = R.sum(axis=1).astype(np.int64)
             a, b = xi2(M, R, C), orc.xi2(M, R, C)
             assert (np.isnan(a) and np.isnan(b)) or a == b, (L, n, a, b)
+
+
+def test_load_rejects_foreign_and_missing_files(abi, tmp_path):
+    lib = abi.lib()
+    h = ctypes.c_void_p()
+    missing = str(tmp_path / "nope.isg").encode()
+    assert lib.isg_load(missing, None, 4, ctypes.byref(h)) == abi.ISG_ERR_INVALID
+    bad = tmp_path / "bad.isg"
+    bad.write_bytes(b"NOTALATT" + bytes(56))
+    assert lib.isg_load(str(bad).encode(), None, 4, ctypes.byref(h)) == abi.ISG_ERR_INVALID
+    assert b"not a lattice checkpoint" in lib.isg_last_error()
+    assert not h.value

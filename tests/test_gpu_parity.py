@@ -203,3 +203,27 @@ def test_invalid_arguments_gpu(isg):
         lat.half_sweep(2, 0.4)
     with pytest.raises(isg.IsgError):
         lat.init_uniform(0)  # 0 is not an Ising spin
+
+
+@pytest.mark.parametrize("model", [0, 1])
+def test_checkpoint_resume_is_bit_exact(isg, tmp_path, model):
+    """n1 sweeps, save, load, n2 sweeps == n1 + n2 sweeps straight."""
+    L, seed = 320, wl.BASE_SEED + 700 + model
+    beta = 0.45 if model == 0 else 0.6
+    straight = isg.Lattice(L, model, seed=seed, delta=0.2, record_capacity=8)
+    straight.init_random()
+    straight.sweep(13, beta=beta)
+    straight.sweep(9, beta=beta, record_every=3)
+    want = straight.read_records()
+    a = isg.Lattice(L, model, seed=seed, delta=0.2)
+    a.init_random()
+    a.sweep(13, beta=beta)
+    path = str(tmp_path / "ckpt.isg")
+    a.save(path)
+    a.close()
+    b = isg.Lattice.load(path, record_capacity=8)
+    assert b.sweep_index == 13 and b.L == L
+    b.sweep(9, beta=beta, record_every=3)
+    got = b.read_records()
+    assert [(r.sweep, r.B, r.M, r.Q) for r in got] == [(r.sweep, r.B, r.M, r.Q) for r in want]
+    assert np.array_equal(b.get(), straight.get())
