@@ -351,6 +351,16 @@ def run_ours(args, w):
         P.xi2([r.M], r.R[None], r.C[None])
     e2e_s = time.perf_counter() - t0
 
+    # axis correlation function C(r) (Eq. (2)) at 12 distances, one pass each
+    corr_r = [1 << k for k in range(12)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sx, sy = lat.correlation(corr_r)
+    corr_s = time.perf_counter() - t0
+    corr = {"distances": corr_r, "ms": 1e3 * corr_s,
+            "lattice_GB_read_per_s": len(corr_r) * 2 * P.Lattice.nbytes(w.model, w.L) / corr_s / 1e9,
+            "C_r": [float(a + b) / (2.0 * float(w.L) ** 2) for a, b in zip(sx, sy)]}
+
     ms, e2e_s = replicas.max_over_ranks([ms, e2e_s], device="cuda")
     sites = float(w.L) * float(w.L)
     value = replicas.weak_scaling_value(world, sites, args.steps, ms)
@@ -387,6 +397,7 @@ def run_ours(args, w):
             "gpu_launches": 3 * args.steps,
             "clocks": clk,
             "xi2_last": xi,
+            "correlation": corr,
         }
         if not args.no_batched and world == 1:
             line["batched"] = batched_bench(sweeps=args.batched_sweeps, n_rep=args.batched_replicas)

@@ -369,6 +369,23 @@ double isg_server_clock(const isg_server *srv);
 isg_status isg_server_stats(const isg_server *srv, double *flips_done, size_t *bytes_in_use,
                             size_t *budget);
 
+/* Correlation function along the axes (Eq. (2)) of the current lattice: for
+ * each distance r[k] (0 <= r[k] < L) the exact sums
+ *   out_x[k] = sum_{x,y} s(x,y) s(x + r[k], y),
+ *   out_y[k] = sum_{x,y} s(x,y) s(x, y + r[k])   (periodic),
+ * so that C(r) = (out_x + out_y) / (2 L^2) averages the two axes and the
+ * energy of Eq. (3) is (out_x + out_y at r = 1) / L^2 up to its sign.  One
+ * pass over the lattice per distance.  Synchronises. */
+isg_status isg_correlation(isg_lattice *lat, int64_t nr, const int64_t *r, int64_t *out_x,
+                           int64_t *out_y);
+
+/* Integral coherence length xi = I2 / I1 (Appendix C), I_n = int_0^{r_cut}
+ * r^n C(r) dr by the trapezoid rule over the n sampled points r[0] < r[1] <
+ * ... (host FP64; points beyond r_cut ignored).  NaN if I1 <= 0 or n < 2.
+ * The paper's choice of r_cut from the errors of C, and its fitted tail
+ * F(r), are analysis steps left to the caller. */
+double isg_xi_integral(int64_t n, const double *r, const double *c, double r_cut);
+
 /* Energy per spin (-B + Delta Q) / L^2 of one record. */
 double isg_energy_density(const isg_obs *obs, int64_t L, double delta);
 

@@ -17,6 +17,8 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*``):
                   beta = infinity limits, global spin-flip symmetry
   measure         pinned: invariants and closed forms on constructed lattices
   xi2             pinned: closed forms on constructed row/column sums
+  correlation     pinned: library FFT autocorrelation, S(1) = B, S(0) = Q,
+                  constructed lattices (tests/test_oracle_correlation.py)
   window_init/run pinned: equal to init_random/run on the interior of the
                   light cone (tests/test_oracle_windows.py)
 """
@@ -63,6 +65,8 @@ def lib():
         L.oracle_run.restype = ctypes.c_int64
         L.oracle_xi2.argtypes = [ctypes.c_int64, ctypes.c_int64, i64p, i32p, i32p]
         L.oracle_xi2.restype = ctypes.c_double
+        L.oracle_correlation.argtypes = [i8p, ctypes.c_int64, ctypes.c_int64, i64p, i64p, i64p]
+        L.oracle_correlation.restype = ctypes.c_int
         L.oracle_window_init.argtypes = [i8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64]
         L.oracle_window_init.restype = ctypes.c_int
@@ -192,3 +196,17 @@ def window_run(s: np.ndarray, y0: int, x0: int, L: int, model: int, seed: int, t
                                  _ptr(betas, ctypes.c_double), float(delta))
     if rc != 0:
         raise ValueError("oracle_window_run rejected its arguments")
+
+
+def correlation(s: np.ndarray, r):
+    """(sx[k], sy[k]) = sums of s(x,y) s(x+r_k,y) and s(x,y) s(x,y+r_k)."""
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    L = s.shape[0]
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.int64).reshape(-1))
+    sx = np.zeros(r.size, dtype=np.int64)
+    sy = np.zeros(r.size, dtype=np.int64)
+    rc = lib().oracle_correlation(_ptr(s, ctypes.c_int8), L, r.size, _ptr(r, ctypes.c_int64),
+                                  _ptr(sx, ctypes.c_int64), _ptr(sy, ctypes.c_int64))
+    if rc != 0:
+        raise ValueError("oracle_correlation rejected its arguments")
+    return sx, sy

@@ -493,3 +493,33 @@ int oracle_window_run(int8_t *s, int64_t h, int64_t w, int64_t y0, int64_t x0, i
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Correlation function along the lattice axes (Eq. (2)).                   */
+/* ------------------------------------------------------------------------ */
+
+/* For each distance r[k] (0 <= r[k] < L): sx[k] = sum_{x,y} s(x,y) s(x+r,y)
+ * and sy[k] = sum_{x,y} s(x,y) s(x,y+r), periodic.  C((r,0)) = sx / L^2 and
+ * C((0,r)) = sy / L^2.                                                     */
+int oracle_correlation(const int8_t *s, int64_t L, int64_t nr, const int64_t *r, int64_t *sx,
+                       int64_t *sy)
+{
+    if (!s || L < 1 || nr < 0 || (nr > 0 && (!r || !sx || !sy)))
+        return -1;
+    for (int64_t k = 0; k < nr; ++k) {
+        if (r[k] < 0 || r[k] >= L)
+            return -1;
+        int64_t ax = 0, ay = 0;
+        for (int64_t y = 0; y < L; ++y) {
+            const int64_t y2 = (y + r[k]) % L;
+            for (int64_t x = 0; x < L; ++x) {
+                const int v = s[y * L + x];
+                ax += v * s[y * L + (x + r[k]) % L];
+                ay += v * s[y2 * L + x];
+            }
+        }
+        sx[k] = ax;
+        sy[k] = ay;
+    }
+    return 0;
+}

@@ -7,7 +7,7 @@ prototypes, ``lattice`` marshals numpy arrays and torch streams into them.
 PyTorch is used only for device memory and streams.
 """
 from ._abi import (ISG_BLUME_CAPEL, ISG_ISING, IsgError, check, lib)  # noqa: F401
-from .lattice import Lattice, Obs, measure_planes_noalloc, xi2  # noqa: F401
+from .lattice import Lattice, Obs, measure_planes_noalloc, xi2, xi_integral  # noqa: F401
 from .ensemble import Ensemble  # noqa: F401
 from .server import Server  # noqa: F401
 

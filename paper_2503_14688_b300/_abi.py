@@ -101,6 +101,8 @@ PROTOTYPES = {
     "isg_measure": (_I32, [_P, ctypes.POINTER(isg_obs)]),
     "isg_measure_planes_noalloc": (_I32, [_I32, _I64, _P, _P, _I64, ctypes.POINTER(isg_obs)]),
     "isg_xi2": (_F64, [_I64, _I64, _I64P, _I32P, _I32P]),
+    "isg_correlation": (_I32, [_P, _I64, _I64P, _I64P, _I64P]),
+    "isg_xi_integral": (_F64, [_I64, _F64P, _F64P, _F64]),
     "isg_energy_density": (_F64, [ctypes.POINTER(isg_obs), _I64, _F64]),
     "isg_last_error": (ctypes.c_char_p, []),
     "isg_ensemble_create": (_I32, [ctypes.POINTER(isg_ensemble_desc), ctypes.POINTER(_P)]),

@@ -584,6 +584,50 @@ isg_status isg_load(const char *path, void *stream, int64_t record_capacity, isg
     return ISG_OK;
 }
 
+isg_status isg_correlation(isg_lattice *lat, int64_t nr, const int64_t *r, int64_t *out_x,
+                           int64_t *out_y)
+{
+    if (!lat || nr < 0 || (nr > 0 && (!r || !out_x || !out_y)) || nr > (1 << 20))
+        return fail(ISG_ERR_INVALID, "bad arguments");
+    for (int64_t k = 0; k < nr; ++k)
+        if (r[k] < 0 || r[k] >= lat->L)
+            return fail(ISG_ERR_INVALID, "distance r[%lld] = %lld outside [0, L)", (long long)k,
+                        (long long)r[k]);
+    if (nr == 0)
+        return ISG_OK;
+    int64_t *d_r = nullptr;
+    unsigned long long *d_out = nullptr;
+    ISG_CUDA(cudaMallocAsync(&d_r, sizeof(int64_t) * nr, lat->stream), "staging allocation");
+    cudaError_t e = cudaMallocAsync(&d_out, sizeof(unsigned long long) * 2 * nr, lat->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_r, r, sizeof(int64_t) * nr, cudaMemcpyHostToDevice, lat->stream);
+    if (e == cudaSuccess)
+        e = cudaMemsetAsync(d_out, 0, sizeof(unsigned long long) * 2 * nr, lat->stream);
+    if (e == cudaSuccess)
+        e = launch_correlation(planes_of(lat), (int)nr, d_r, d_out, lat->stream);
+    std::vector<int64_t> h((size_t)(2 * nr));
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.data(), d_out, sizeof(int64_t) * 2 * nr, cudaMemcpyDeviceToHost,
+                            lat->stream);
+    cudaFreeAsync(d_r, lat->stream);
+    if (d_out)
+        cudaFreeAsync(d_out, lat->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(lat->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "correlation");
+    for (int64_t k = 0; k < nr; ++k) {
+        out_x[k] = h[(size_t)k];
+        out_y[k] = h[(size_t)(nr + k)];
+    }
+    return ISG_OK;
+}
+
+double isg_xi_integral(int64_t n, const double *r, const double *c, double r_cut)
+{
+    return xi_integral_fp64(n, r, c, r_cut);
+}
+
 double isg_xi2(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const int32_t *C)
 {
     return xi2_fp64(n, L, M, R, C);

@@ -174,4 +174,24 @@ double xi2_fp64(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const 
     return std::sqrt(s0avg / skavg - 1.0) / (2.0 * std::sin(M_PI / (double)L));
 }
 
+// Integral coherence length (Appendix C): xi = I2 / I1 with
+// I_n = int_0^{r_cut} r^n C(r) dr, by the trapezoid rule over the sampled
+// distances r[0] < r[1] < ... (those beyond r_cut are ignored).
+double xi_integral_fp64(int64_t n, const double *r, const double *c, double r_cut)
+{
+    if (n < 2 || !r || !c)
+        return NAN;
+    double i1 = 0.0, i2 = 0.0;
+    for (int64_t k = 1; k < n && r[k] <= r_cut; ++k) {
+        const double h = r[k] - r[k - 1];
+        if (!(h > 0.0))
+            return NAN;
+        i1 += 0.5 * h * (r[k - 1] * c[k - 1] + r[k] * c[k]);
+        i2 += 0.5 * h * (r[k - 1] * r[k - 1] * c[k - 1] + r[k] * r[k] * c[k]);
+    }
+    if (!(i1 > 0.0))
+        return NAN;
+    return i2 / i1;
+}
+
 }  // namespace isg

@@ -66,6 +66,7 @@ void philox_launch_consts(uint64_t seed, uint32_t w2, uint32_t w3, PhiloxLaunch 
 void ising_thresholds(double beta, IsingThr *out);
 void bc_table(double beta, double delta, BcTable *out);
 double xi2_fp64(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const int32_t *C);
+double xi_integral_fp64(int64_t n, const double *r, const double *c, double r_cut);
 
 // ---- error reporting shared by the C-ABI files (isg_api.cu) ----
 // Stores a printf-style message for isg_last_error() and returns code.
@@ -78,6 +79,8 @@ cudaError_t launch_init_uniform(const Planes &pl, int value, cudaStream_t st);
 cudaError_t launch_half_sweep(const Planes &pl, int colour, const PhiloxLaunch &ph,
                               const IsingThr &ithr, const BcTable *btab, cudaStream_t st);
 cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaStream_t st);
+cudaError_t launch_correlation(const Planes &pl, int nr, const int64_t *d_r, unsigned long long *d_out,
+                               cudaStream_t st);
 cudaError_t launch_pack(const Planes &pl, const int8_t *d_spins, int32_t *d_bad, cudaStream_t st);
 cudaError_t launch_unpack_rect(const Planes &pl, int64_t y0, int64_t x0, int64_t h, int64_t w,
                                int8_t *d_out, cudaStream_t st);

@@ -533,6 +533,97 @@ __global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
 }
 
 // ---------------------------------------------------------------------------
+// Correlation function along the axes (Eq. (2)): for each distance r of a
+// list, Sx(r) = sum s(x,y) s(x+r,y) and Sy(r) = sum s(x,y) s(x,y+r), exact.
+// A thread owns one word column w of one colour plane c over a band of rows.
+//   vertical:   the partner of (c, y, w) is word w of row y+r in plane
+//               c ^ (r & 1) (same same-colour index);
+//   horizontal: the partner row is row y of plane c ^ (r & 1), shifted by
+//               k = r/2 sites (r even) or (r-1)/2 + p (r odd, p = (c^y) & 1),
+//               taken with a funnel shift across the word boundary.
+// A pair contributes s s' = 1 - 2 [bits differ] (Ising) or
+// n n' (1 - 2 (p ^ p')) (Blume-Capel), counted with popcounts.
+// ---------------------------------------------------------------------------
+template <int MODEL>
+__device__ __forceinline__ int pair_sum(uint32_t an, uint32_t ap, uint32_t bn, uint32_t bp)
+{
+    if (MODEL == 0)
+        return 32 - 2 * __popc(ap ^ bp);
+    const uint32_t both = an & bn;
+    return __popc(both) - 2 * __popc(both & (ap ^ bp));
+}
+
+template <int MODEL>
+__global__ void __launch_bounds__(kMeasureThreads)
+    k_correlation(Planes pl, int H, int nr, const int64_t *__restrict__ rlist,
+                  unsigned long long *__restrict__ out)
+{
+    const int64_t L = pl.L, W = pl.W, LW = L * W;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = gid < 2 * W;
+    const int c = active ? (int)(gid / W) : 0;
+    const int64_t w = active ? gid - (int64_t)c * W : 0;
+    const int64_t y0 = (int64_t)blockIdx.y * H;
+    const int64_t y1 = y0 + H < L ? y0 + H : L;
+    const int64_t half = L / 2;
+    // sign plane (Ising: the only plane) and occupancy plane of colour cc
+    auto sgn = [&](int cc) { return pl.base + (MODEL == 0 ? cc : 2 * cc + 1) * LW; };
+    auto occ = [&](int cc) { return pl.base + (2 * cc) * LW; };
+    __shared__ long long s_red[2][kMeasureThreads / 32];
+    for (int k = 0; k < nr; ++k) {
+        const int64_t r = rlist[k];
+        const int cp = c ^ (int)(r & 1);
+        int ax = 0, ay = 0;
+        if (active) {
+            const uint32_t *os = sgn(c), *on = occ(c), *ps = sgn(cp), *pn = occ(cp);
+            for (int64_t y = y0; y < y1; ++y) {
+                const uint32_t a_p = __ldg(os + y * W + w);
+                const uint32_t a_n = MODEL == 1 ? __ldg(on + y * W + w) : 0u;
+                // vertical partner
+                int64_t yv = y + r;
+                if (yv >= L)
+                    yv -= L;
+                const uint32_t v_p = __ldg(ps + yv * W + w);
+                const uint32_t v_n = MODEL == 1 ? __ldg(pn + yv * W + w) : 0u;
+                ay += pair_sum<MODEL>(a_n, a_p, v_n, v_p);
+                // horizontal partner: bits i + kk of row y of plane cp
+                int64_t kk = (r & 1) ? (r - 1) / 2 + ((c ^ (int)y) & 1) : r / 2;
+                if (kk >= half)
+                    kk -= half;
+                int64_t w1 = w + (kk >> 5);
+                if (w1 >= W)
+                    w1 -= W;
+                const int64_t w2 = w1 + 1 == W ? 0 : w1 + 1;
+                const unsigned o = (unsigned)(kk & 31);
+                const uint32_t h_p = __funnelshift_r(__ldg(ps + y * W + w1), __ldg(ps + y * W + w2), o);
+                const uint32_t h_n = MODEL == 1
+                                         ? __funnelshift_r(__ldg(pn + y * W + w1), __ldg(pn + y * W + w2), o)
+                                         : 0u;
+                ax += pair_sum<MODEL>(a_n, a_p, h_n, h_p);
+            }
+        }
+        long long sx = __reduce_add_sync(0xFFFFFFFFu, ax);
+        long long sy = __reduce_add_sync(0xFFFFFFFFu, ay);
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        if (lane == 0) {
+            s_red[0][warp] = sx;
+            s_red[1][warp] = sy;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long tx = 0, ty = 0;
+            for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+                tx += s_red[0][i];
+                ty += s_red[1][i];
+            }
+            atomicAdd(&out[k], (unsigned long long)tx);
+            atomicAdd(&out[nr + k], (unsigned long long)ty);
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Byte-per-site <-> planes.
 // ---------------------------------------------------------------------------
 __global__ void k_pack(Planes pl, const int8_t *__restrict__ s, int32_t *bad)
@@ -691,6 +782,21 @@ cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaSt
         k_measure<0><<<grid, kMeasureThreads, 0, st>>>(pl, (int)H, hdr, R, C, sweep);
     else
         k_measure<1><<<grid, kMeasureThreads, 0, st>>>(pl, (int)H, hdr, R, C, sweep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_correlation(const Planes &pl, int nr, const int64_t *d_r, unsigned long long *d_out,
+                               cudaStream_t st)
+{
+    const int64_t bx = (2 * pl.W + kMeasureThreads - 1) / kMeasureThreads;
+    int64_t H = pl.L < 4096 ? pl.L : 4096;
+    while (H > 1 && bx * ((pl.L + H - 1) / H) < 148 * 8)
+        H >>= 1;
+    const dim3 grid((unsigned)bx, (unsigned)((pl.L + H - 1) / H));
+    if (pl.model == 0)
+        k_correlation<0><<<grid, kMeasureThreads, 0, st>>>(pl, (int)H, nr, d_r, d_out);
+    else
+        k_correlation<1><<<grid, kMeasureThreads, 0, st>>>(pl, (int)H, nr, d_r, d_out);
     return cudaGetLastError();
 }
 

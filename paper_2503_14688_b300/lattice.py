@@ -176,6 +176,15 @@ class Lattice:
                     R[i] if with_sums else None, C[i] if with_sums else None)
                 for i in range(cnt.value)]
 
+    def correlation(self, r):
+        """(Sx[k], Sy[k]): axis correlation sums at distances r[k] (isg_correlation)."""
+        r = np.ascontiguousarray(np.asarray(r, dtype=np.int64).reshape(-1))
+        sx = np.zeros(r.size, dtype=np.int64)
+        sy = np.zeros(r.size, dtype=np.int64)
+        check(self._lib.isg_correlation(self._h, r.size, r.ctypes.data_as(_abi._I64P),
+                                        sx.ctypes.data_as(_abi._I64P), sy.ctypes.data_as(_abi._I64P)))
+        return sx, sy
+
     def measure(self) -> Obs:
         R = np.zeros(self.L, dtype=np.int32)
         C = np.zeros(self.L, dtype=np.int32)
@@ -210,3 +219,11 @@ def measure_planes_noalloc(model: int, L: int, planes, stream=None, sweep: int =
     check(lib().isg_measure_planes_noalloc(int(model), int(L), ptr, _stream_handle(stream),
                                            int(sweep), ctypes.byref(o)))
     return Obs(o.sweep, o.B, o.M, o.Q, R, C)
+
+
+def xi_integral(r, c, r_cut: float) -> float:
+    """xi = I2/I1 of a sampled C(r) up to r_cut (isg_xi_integral)."""
+    r = np.ascontiguousarray(np.asarray(r, dtype=np.float64))
+    c = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
+    return float(lib().isg_xi_integral(r.size, r.ctypes.data_as(_abi._F64P),
+                                       c.ctypes.data_as(_abi._F64P), float(r_cut)))

@@ -103,3 +103,20 @@ def test_load_rejects_foreign_and_missing_files(abi, tmp_path):
     assert lib.isg_load(str(bad).encode(), None, 4, ctypes.byref(h)) == abi.ISG_ERR_INVALID
     assert b"not a lattice checkpoint" in lib.isg_last_error()
     assert not h.value
+
+
+def test_xi_integral_closed_forms(abi):
+    """C(r) = exp(-r/a): I2/I1 -> 2a (continuum); C = const: I2/I1 = (2/3) r_cut."""
+    import math
+
+    from paper_2503_14688_b300 import xi_integral
+
+    r = np.linspace(0.0, 400.0, 40001)
+    for a in (3.0, 10.0, 25.0):
+        assert abs(xi_integral(r, np.exp(-r / a), 400.0) - 2 * a) < 1e-4 * a
+    rc = np.arange(0.0, 101.0)
+    assert abs(xi_integral(rc, np.ones_like(rc), 100.0) - 2 / 3 * 100.0) < 0.01
+    # points beyond r_cut are ignored; degenerate input gives NaN
+    assert abs(xi_integral(rc, np.ones_like(rc), 50.0) - 2 / 3 * 50.0) < 0.01
+    assert math.isnan(xi_integral([0.0], [1.0], 10.0))
+    assert math.isnan(xi_integral(rc, -np.ones_like(rc), 100.0))

@@ -66,6 +66,10 @@ def test_full_size_light_cone_and_sums(isg, orc, which):
         for x in rng.integers(0, L, size=3):
             col = lat.get_rect(0, int(x), L, 1)
             assert int(col.astype(np.int64).sum()) == int(rec.C[x])
+        # the axis correlation sums at full size: S(0) = Q, Sx(1) + Sy(1) = B
+        sx, sy = lat.correlation([0, 1, 2, 1000])
+        assert sx[0] == rec.Q and sy[0] == rec.Q
+        assert sx[1] + sy[1] == rec.B
         # isg_measure on the same state equals the record
         o = lat.measure()
         assert (o.B, o.M, o.Q) == (rec.B, rec.M, rec.Q)

@@ -227,3 +227,22 @@ def test_checkpoint_resume_is_bit_exact(isg, tmp_path, model):
     got = b.read_records()
     assert [(r.sweep, r.B, r.M, r.Q) for r in got] == [(r.sweep, r.B, r.M, r.Q) for r in want]
     assert np.array_equal(b.get(), straight.get())
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("L", [64, 192, 256, 1024])
+def test_correlation_matches_oracle(isg, orc, model, L):
+    """Axis correlation sums (Eq. (2)) on an evolved lattice, all parities of
+    r, the wrap-around distances and r = 0, bit-exact."""
+    seed = wl.BASE_SEED + 800 + L + model
+    lat, s = _pair(isg, orc, model, L, seed, delta=0.3)
+    beta = 0.44 if model == 0 else 0.6
+    lat.sweep(7, beta=beta)
+    orc.run(s, model, seed, 0, [beta] * 7, delta=0.3)
+    r = sorted(set([0, 1, 2, 3, 5, 31, 32, 33, 63, L // 2 - 1, L // 2, L // 2 + 1, L - 1]) &
+               set(range(L)))
+    gx, gy = lat.correlation(r)
+    ox, oy = orc.correlation(s, r)
+    assert np.array_equal(gx, ox) and np.array_equal(gy, oy)
+    o = lat.measure()
+    assert gx[r.index(1)] + gy[r.index(1)] == o.B and gx[0] == o.Q

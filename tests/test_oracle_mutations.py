@@ -35,6 +35,9 @@ MUTATIONS = {
         ["test_oracle_observables.py"]),
     "Philox key increment": (
         "k[1] += 0xBB67AE85u;", "k[1] += 0xBB67AE84u;", ["test_oracle_philox.py"]),
+    "correlation partner off by one": (
+        "ax += v * s[y * L + (x + r[k]) % L];", "ax += v * s[y * L + (x + r[k] + 1) % L];",
+        ["test_oracle_correlation.py"]),
     "hot-start bias": (
         "s[idx] = (int8_t)(u >= 0x80000000u ? 1 : -1);",
         "s[idx] = (int8_t)(u >= 0x7F000000u ? 1 : -1);",
