@@ -86,3 +86,38 @@ def test_critical_u4_and_xi2_over_L(isg, model, beta):
     assert abs(xi - XI_STAR) < 4 * dxi + 0.006, (xi, dxi)
     # sanity: the errors are small enough for the check to mean something
     assert du4 < 0.002 and dxi < 0.004
+
+
+@pytest.mark.parametrize("model,beta", [(wl.ISING, wl.BETA_C_ISING),
+                                        (wl.BLUME_CAPEL, 1.0 / wl.T_C_BLUME_CAPEL)])
+def test_quench_coherence_length_grows_as_t_to_the_1_over_z(isg, model, beta):
+    """Direct quench to T_c ("Thermal protocols"): the coherence length
+    xi(t) = I2/I1 from the axis correlation function (Eq. (2), Appendix C)
+    grows as t^(1/z), z = 2.1676(1) (Results), the same for both models.
+    Loose check on one L = 16384 lattice (L/xi > 100, so no finite-size
+    effect) over t = 128..2048, cutoff at C(r) < 0.005; for Ising the energy
+    excess E(t) - E_eq = 2 (sqrt(2)/2 - C(1)) per spin decays with the same
+    exponent (Eq. (4))."""
+    L = 16384
+    lat = isg.Lattice(L, model, seed=wl.BASE_SEED + 4242)
+    lat.init_random()
+    r = np.arange(0, 400)
+    ts, xis, c1 = [128, 256, 512, 1024, 2048], [], []
+    prev = 0
+    for t in ts:
+        lat.sweep(t - prev, beta=beta)
+        prev = t
+        sx, sy = lat.correlation(r)
+        C = (sx + sy) / (2.0 * L * L)
+        cut = int(np.argmax(C[1:] < 0.005)) + 1
+        assert C[cut] < 0.005 and cut > 10
+        xis.append(isg.xi_integral(r[:cut + 1].astype(float), C[:cut + 1], float(cut)))
+        c1.append(C[1])
+    lat.close()
+    slope = np.polyfit(np.log(ts), np.log(xis), 1)[0]
+    assert 0.42 < slope < 0.50, (slope, xis)          # 1/z = 0.4613
+    if model == wl.ISING:
+        excess = math.sqrt(2) / 2 - np.array(c1)
+        assert np.all(excess > 0)
+        s_e = -np.polyfit(np.log(ts), np.log(excess), 1)[0]
+        assert 0.42 < s_e < 0.52, s_e
