@@ -36,13 +36,18 @@ from paper_2503_14688_b300 import workloads as wl  # noqa: E402
 METRIC = "spin flips/ns per B300 (Ising, BC) & % roofline; batched/served vs single lattice"
 UNIT = "flips/ns"
 
-# Algorithmic integer operations per site update (roofline):
+# Algorithmic integer operations per site update:
 # Philox4x32-10 per 4 sites = 20 wide multiplies + 20 three-input XORs;
 # the acceptance compares: Ising 2 per site, Blume-Capel 1 per site plus the
 # proposal bit.  Units: one 32-lane-issue integer operation.
 ALG_OPS_PER_SITE = {wl.ISING: 10.0 + 2.0, wl.BLUME_CAPEL: 10.0 + 2.0}
 SMS = 148
 INT_LANES_PER_SM = 128     # 4 SMSPs x 32 lanes, one warp-instruction per SMSP per clock
+# The pipe that binds the half-sweep: the 32x32->64 multiplies of Philox run
+# on the FMA-heavy pipe at 32 per SM per clock (calibrated on a B300, half
+# the rate of a 32-bit multiply-add); the sweep needs 18 per 4 sites.
+WIDE_MUL_PER_SM_CLK = 32
+WIDE_MUL_PER_SITE = 18 / 4
 
 
 def _peaks():
@@ -372,6 +377,7 @@ def run_ours(args, w):
     dom_ms = statistics.mean(dom)
     ops = ALG_OPS_PER_SITE[w.model] * sites / 2
     achieved = ops / (dom_ms * 1e-3) / 1e12
+    wide_bound = SMS * WIDE_MUL_PER_SM_CLK / WIDE_MUL_PER_SITE * sm_max * 1e6 / 1e9
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -391,7 +397,13 @@ def run_ours(args, w):
                          "ops_per_site": ALG_OPS_PER_SITE[w.model],
                          "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int lanes x "
                                        f"{sm_max:.0f} MHz ({peak_src})",
-                         "half_sweep_ms": [statistics.mean(half0), statistics.mean(half1)]},
+                         "half_sweep_ms": [statistics.mean(half0), statistics.mean(half1)],
+                         "wide_multiply_bound": {
+                             "basis": f"{WIDE_MUL_PER_SITE} wide multiplies per site at "
+                                      f"{WIDE_MUL_PER_SM_CLK} per SM per clock (FMA-heavy pipe)",
+                             "sites_per_ns": wide_bound,
+                             "achieved_sites_per_ns": sites / 2 / (dom_ms * 1e6),
+                             "frac": sites / 2 / (dom_ms * 1e6) / wide_bound}},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8,
                     "d2h_bytes_per_step": 32 + 8 * w.L, "steps": e2e_steps},
             "gpu_launches": 3 * args.steps,

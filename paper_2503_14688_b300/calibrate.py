@@ -16,7 +16,13 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(PKG, "libisg_calib.so")
 
 KINDS = {0: ("mul.wide (32x32->64) + xor", 8), 1: ("mul.hi + xor", 8), 2: ("mad.lo", 8),
-         3: ("xor3", 8), 4: ("add3", 8), 5: ("philox4x32-10 call", 2)}
+         3: ("xor3", 8), 4: ("add3", 8), 5: ("philox4x32-10 call", 2),
+         6: ("compare by sub.cc + addc", 8), 7: ("funnel shift", 8), 8: ("shift + or (C)", 8),
+         9: ("add", 8), 10: ("byte permute", 8), 11: ("compare accumulated in C", 8),
+         12: ("compare by borrow logic + funnel shift", 8),
+         13: ("Ising word update, per site", 32), 14: ("sweep Philox call (folded)", 8),
+         15: ("sweep Philox call, not unrolled", 8), 16: ("sweep Philox call, 4 per step", 4),
+         17: ("sweep Philox call, 128 registers", 8), 18: ("Philox call unfolded, 8 unrolled", 8)}
 
 
 def sm_clock_mhz():
@@ -43,7 +49,7 @@ def main():
     sink = torch.zeros(blocks, dtype=torch.int32, device="cuda")
     res = {"sms": sms, "blocks": blocks, "threads": threads, "kinds": {}}
     for kind, (name, per_iter) in KINDS.items():
-        iters = 20000 if kind != 5 else 2000
+        iters = {5: 2000, 13: 400, 14: 400, 15: 400, 16: 400, 17: 400, 18: 400}.get(kind, 20000)
         lib.isg_calib_run(kind, blocks, threads, 100, sink.data_ptr())  # warm-up
         mhz0 = sm_clock_mhz()
         ms = lib.isg_calib_run(kind, blocks, threads, iters, sink.data_ptr())

@@ -63,20 +63,18 @@ __device__ __forceinline__ uint32_t ising_word_update(uint32_t t, uint32_t up, u
                                                       const PhiloxLaunch &pc, const IsingThr &thr)
 {
     const PhiloxWordPart wp = philox_word_part(pc, (uint32_t)(q0 >> 32));
-    // reject masks: bit 4i+k set iff site 4i+k's word >= the threshold
+    // reject masks, bit b set iff site b's word >= the threshold: one chain
+    // over the 32 sites, site 31 first, so no per-call merge is needed
     uint32_t r4 = 0, r8 = 0;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 7; i >= 0; --i) {
         uint32_t r[4];
         philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
-        uint32_t n4 = 0, n8 = 0;
 #pragma unroll
         for (int k = 3; k >= 0; --k) {
-            n4 = shift_in_not_below(n4, r[k], thr.thr4);
-            n8 = shift_in_not_below(n8, r[k], thr.thr8);
+            r4 = shift_in_not_below(r4, r[k], thr.thr4);
+            r8 = shift_in_not_below(r8, r[k], thr.thr8);
         }
-        r4 = n4 * (1u << (4 * i)) + r4;
-        r8 = n8 * (1u << (4 * i)) + r8;
     }
     const uint32_t a4 = ~r4 | thr.full4;
     const uint32_t a8 = ~r8 | thr.full8;
