@@ -48,6 +48,19 @@ INT_LANES_PER_SM = 128     # 4 SMSPs x 32 lanes, one warp-instruction per SMSP p
 # the rate of a 32-bit multiply-add); the sweep needs 18 per 4 sites.
 WIDE_MUL_PER_SM_CLK = 32
 WIDE_MUL_PER_SITE = 18 / 4
+# DRAM bytes (read + write) per site of one half-sweep launch, from one ncu
+# capture of the current kernels on a smaller lattice (Ising L = 2^16:
+# 536.9 + 229.4 MB per 2^31 sites; Blume-Capel L = 2^15: 268.5 + 95.9 MB per
+# 2^29 sites), scaled to a full launch by the sites it updates.  Against the
+# algorithmic 0.375 (Ising) and 0.75 (Blume-Capel) B per site.
+DRAM_BYTES_PER_SITE = {wl.ISING: (536.9e6 + 229.4e6) / 2**31,
+                       wl.BLUME_CAPEL: (268.5e6 + 95.9e6) / 2**29}
+
+
+def _l2_note(lattice_bytes):
+    if lattice_bytes > 2 * 126e6:
+        return "not needed: lattice %.1f GiB >> 126 MB L2" % (lattice_bytes / 2**30)
+    return "none: lattice %.1f MiB may stay in the 126 MB L2" % (lattice_bytes / 2**20)
 
 
 def _peaks():
@@ -387,12 +400,16 @@ def run_ours(args, w):
             "config": {"workload": w.name, "model": "ising" if w.model == 0 else "blume_capel",
                        "L": w.L, "spins": int(sites), "beta": beta, "delta": w.delta,
                        "parallelism": "replicas" if world > 1 else "single",
-                       "l2_flush": "not needed: lattice %.0f GiB >> 126 MB L2"
-                                   % (P.Lattice.nbytes(w.model, w.L) / 2**30),
+                       "l2_flush": _l2_note(P.Lattice.nbytes(w.model, w.L)),
                        "step": "host thresholds + half-sweep colour 0 + half-sweep colour 1 "
                                "+ on-device record of B, M, Q, row and column sums"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak,
+                         "traffic": DRAM_BYTES_PER_SITE[w.model] * sites / 2,
+                         "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
+                                          "one half-sweep at L=2^16 (Ising) / 2^15 (Blume-Capel), "
+                                          "scaled by sites per launch; algorithmic "
+                                          f"{0.375 if w.model == wl.ISING else 0.75} B/site",
                          "kernel": "half-sweep colour %d" % (1 if dom is half1 else 0),
                          "ops_per_site": ALG_OPS_PER_SITE[w.model],
                          "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int lanes x "
