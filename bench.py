@@ -200,6 +200,26 @@ def batched_bench(sweeps=10000, n_rep=4096, record_every=1000):
             "ratio_vs_single": batched / single}
 
 
+def precool_bench(n_rep=4096):
+    """The pre-cooling scan at scaled size (Ising, T1 = 0.73 T_c, T2 = 1.04 T_c,
+    L = 512 replicas): xi_eq(T2), the switch times, the protocol ensembles for
+    four f and the joint fit of Eq. (8); the zero f* of b(f) against the
+    paper's 0.59(5)."""
+    from paper_2503_14688_b300 import precooling as pc
+
+    t0 = time.perf_counter()
+    res = pc.scan(wl.ISING, [0.3, 0.45, 0.6, 0.75], n_replicas=n_rep, n_xi=16, t_after=1000)
+    return {"workload": "Ising pre-cooling scan: T1 = 0.73 T_c, T2 = 1.04 T_c, %d replicas of "
+                        "L = 512, f in {0.3, 0.45, 0.6, 0.75}, 1000 sweeps at T2" % n_rep,
+            "xi_eq": res["xi_eq"], "t_switch": res["t_switch"], "tau": res["fit"]["tau"],
+            "b": res["fit"]["b"], "b_err": res["fit"]["b_err"],
+            "fit_window": [res["fit"]["t_min"], res["fit"]["t_max"]],
+            "chi2_per_dof": res["fit"]["chi2_per_dof"],
+            "f_star": res["f_star"], "f_star_err": res["f_star_err"], "f_star_paper": 0.59,
+            "ensemble_flips_per_ns": res["ensemble_flips_per_ns"],
+            "seconds": time.perf_counter() - t0}
+
+
 def served_bench(n_req=48, load=0.9, chunk=100, max_active=48):
     """The served stream: requests of the served workload (workloads.py)
     through the continuous-batching server.  First all at once (capacity and
@@ -431,6 +451,8 @@ def run_ours(args, w):
         if not args.no_batched and world == 1:
             line["batched"] = batched_bench(sweeps=args.batched_sweeps, n_rep=args.batched_replicas)
             line["served"] = served_bench(n_req=args.served_requests)
+        if not args.no_precool and world == 1:
+            line["precool"] = precool_bench()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w.model, beta, w.delta)
         print(json.dumps(line), flush=True)
@@ -447,6 +469,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ising_large")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precool", action="store_true",
+                    help="skip the pre-cooling scan (Eq. (8)) sub-object")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the replica-ensemble measurement")
     ap.add_argument("--L", type=int, default=0, help="override the workload's L (profiling)")

@@ -97,6 +97,21 @@ class Ensemble:
             out.append(row)
         return out
 
+    def read_scalars(self, rows: Optional[int] = None):
+        """Up to `rows` oldest record rows without the row and column sums, as
+        arrays: (sweep[k], B[k, n], M[k, n], Q[k, n]) (int64)."""
+        k = self.info()["pending"] if rows is None else int(rows)
+        empty = np.zeros((0, self.n), dtype=np.int64)
+        if k == 0:
+            return np.zeros(0, dtype=np.int64), empty, empty.copy(), empty.copy()
+        obs = (_abi.isg_obs * (k * self.n))()
+        cnt = ctypes.c_int64()
+        check(self._lib.isg_ensemble_read_records(self._h, k, obs, ctypes.byref(cnt)))
+        # isg_obs: four int64 (sweep, B, M, Q) then two pointers, 48 bytes
+        raw = np.frombuffer(obs, dtype=np.int64).reshape(k, self.n, ctypes.sizeof(_abi.isg_obs) // 8)
+        raw = raw[: cnt.value]
+        return raw[:, 0, 0].copy(), raw[:, :, 1].copy(), raw[:, :, 2].copy(), raw[:, :, 3].copy()
+
     def get(self, r: int) -> np.ndarray:
         L = int(self.L[r])
         out = np.empty((L, L), dtype=np.int8)
