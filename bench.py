@@ -50,11 +50,11 @@ WIDE_MUL_PER_SM_CLK = 32
 WIDE_MUL_PER_SITE = 18 / 4
 # DRAM bytes (read + write) per site of one half-sweep launch, from one ncu
 # capture of the current kernels on a smaller lattice (Ising L = 2^16:
-# 536.9 + 229.4 MB per 2^31 sites; Blume-Capel L = 2^15: 268.5 + 95.9 MB per
+# 536.9 + 229.4 MB per 2^31 sites; Blume-Capel L = 2^15: 274.1 + 93.6 MB per
 # 2^29 sites), scaled to a full launch by the sites it updates.  Against the
 # algorithmic 0.375 (Ising) and 0.75 (Blume-Capel) B per site.
 DRAM_BYTES_PER_SITE = {wl.ISING: (536.9e6 + 229.4e6) / 2**31,
-                       wl.BLUME_CAPEL: (268.5e6 + 95.9e6) / 2**29}
+                       wl.BLUME_CAPEL: (274.1e6 + 93.6e6) / 2**29}
 
 
 def _l2_note(lattice_bytes):

@@ -33,7 +33,7 @@ namespace {
 constexpr int kSweepThreads = 128;
 constexpr int kSweepMinBlocks = 10;  // 48 registers: 40 warps per SM
 constexpr int kBcThreads = 256;
-constexpr int kBcMinBlocks = 3;      // 85 registers: 24 warps per SM
+constexpr int kBcMinBlocks = 3;      // 80 registers: 24 warps per SM
 constexpr int kMeasureThreads = 256;
 
 template <int V>
@@ -684,10 +684,14 @@ __global__ void k_unpack_rect(Planes pl, int64_t y0, int64_t x0, int64_t h, int6
 }
 
 // Rows per thread for a sweep launch: at most 64, fewer while the grid would
-// give less than about eight waves of resident blocks (tail balance).
-int sweep_band(int64_t L, int64_t threads_per_row)
+// give less than `waves` waves of resident blocks (blocks_per_sm blocks of
+// `threads` threads on each of the 148 SMs).  Ising: eight waves of its
+// 128-thread blocks; Blume-Capel: two waves of its 256-thread blocks (taller
+// bands: at L = 16384, 919 vs 830 flips/ns with the Ising rule).
+int sweep_band(int64_t L, int64_t threads_per_row, int blocks_per_sm = kSweepMinBlocks,
+               int threads = kSweepThreads, int waves = 8)
 {
-    const int64_t want_threads = 148LL * kSweepMinBlocks * 8 * kSweepThreads;
+    const int64_t want_threads = 148LL * blocks_per_sm * threads * waves;
     int H = 64;
     while (H > 1 && threads_per_row * ((L + H - 1) / H) < want_threads)
         H >>= 1;
@@ -723,7 +727,7 @@ cudaError_t launch_bc(const Planes &pl, int colour, const PhiloxLaunch &ph, cons
     const uint32_t *nn = pl.base + (int64_t)(2 * (1 - colour)) * LW;
     const uint32_t *np = nn + LW;
     const int64_t tpr = pl.W / V;
-    const int H = sweep_band(pl.L, tpr);
+    const int H = sweep_band(pl.L, tpr, kBcMinBlocks, kBcThreads, 2);
     const int64_t threads = tpr * ((pl.L + H - 1) / H);
     k_bc_half<V><<<(unsigned)((threads + kBcThreads - 1) / kBcThreads), kBcThreads, 0, st>>>(
         tn, tp, nn, np, pl.L, pl.W, colour, H, ph, tab);
@@ -758,9 +762,10 @@ cudaError_t launch_half_sweep(const Planes &pl, int colour, const PhiloxLaunch &
             return launch_ising<2>(pl, colour, ph, ithr, st);
         return launch_ising<1>(pl, colour, ph, ithr, st);
     }
-    if (V == 4)
-        return launch_bc<4>(pl, colour, ph, *btab, st);
-    if (V == 2)
+    // Blume-Capel: two words per thread (more threads in flight than four
+    // at the same 80 registers: 137 vs 148 ms per half-sweep at L = 2^19,
+    // 919 vs 898 flips/ns at L = 16384)
+    if (V >= 2)
         return launch_bc<2>(pl, colour, ph, *btab, st);
     return launch_bc<1>(pl, colour, ph, *btab, st);
 }
