@@ -1,0 +1,109 @@
+"""Parity of the replica-ensemble workload in the launch configuration the
+benchmark times: 4096 Ising replicas with L drawn from {64, ..., 1024},
+seeds base + 3 + r, hot start at beta_c, CTA size autotuned, 4 warm-up
+sweeps, then 10^4 sweeps in one persistent launch with records every 1000.
+
+* every replica: its record after the first 100 sweeps (B, M, Q, R, C) equals
+  the record of the same lattice swept alone;
+* sampled replicas of L = 64, 128, 256 after all 10^4 sweeps: final spins
+  and all ten records equal the oracle's, run from the oracle's own hot start;
+* sampled replicas of L = 512, 1024: final spins and records equal the
+  lattice swept alone (itself oracle-checked in test_gpu_parity.py);
+* the ensemble-mean xi_2 over the oracle-checked replicas equals the
+  oracle's (bitwise: same integers, same FP64 order).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2503_14688_b300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+N_REP, SWEEPS, EVERY, WARM = 4096, 10000, 1000, 4
+
+
+@pytest.fixture(scope="module")
+def isg():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA GPU")
+    from paper_2503_14688_b300 import build
+
+    build.build()
+    import paper_2503_14688_b300 as P
+
+    return P
+
+
+def _same(a, b):
+    assert (a.sweep, a.B, a.M, a.Q) == (b.sweep, b.B, b.M, b.Q)
+    assert np.array_equal(a.R, b.R) and np.array_equal(a.C, b.C)
+
+
+def test_all_replicas_first_100_sweeps(isg):
+    Ls = wl.ensemble_sizes(N_REP)
+    seeds = [wl.BASE_SEED + 3 + r for r in range(N_REP)]
+    ens = isg.Ensemble(Ls, seeds, record_capacity=2)
+    ens.init_random()
+    ens.autotune(4)
+    ens.sweep(100, beta=wl.BETA_C_ISING, record_every=100)
+    (row,) = ens.read_records()
+    ens.close()
+    for r in range(N_REP):
+        lat = isg.Lattice(int(Ls[r]), wl.ISING, seed=seeds[r], record_capacity=1)
+        lat.init_random()
+        lat.sweep(100, beta=wl.BETA_C_ISING, record_every=100)
+        (rec,) = lat.read_records()
+        lat.close()
+        _same(row[r], rec)
+
+
+def test_bench_configuration_sampled_replicas(isg, orc):
+    Ls = wl.ensemble_sizes(N_REP)
+    seeds = [wl.BASE_SEED + 3 + r for r in range(N_REP)]
+    ens = isg.Ensemble(Ls, seeds, record_capacity=SWEEPS // EVERY + 1)
+    ens.init_random()
+    assert ens.autotune(4) in (256, 512, 1024)
+    ens.sweep(WARM, beta=wl.BETA_C_ISING)
+    ens.sweep(SWEEPS, beta=wl.BETA_C_ISING, record_every=EVERY)
+    rows = ens.read_records()
+    assert [row[0].sweep for row in rows] == [WARM + EVERY * k for k in range(1, SWEEPS // EVERY + 1)]
+    pick = {L: [r for r in range(N_REP) if Ls[r] == L][:3] for L in (64, 128, 256, 512, 1024)}
+    threads = os.cpu_count() or 1
+    betas = [wl.BETA_C_ISING] * SWEEPS
+    M, R, C = [], [], []
+    for L in (64, 128, 256):
+        for r in pick[L]:
+            s = orc.init_random(L, wl.ISING, seeds[r])
+            orc.run(s, wl.ISING, seeds[r], 0, [wl.BETA_C_ISING] * WARM, nthreads=threads)
+            bmq, Ro, Co = orc.run(s, wl.ISING, seeds[r], WARM, betas, record_every=EVERY,
+                                  nthreads=threads)
+            assert np.array_equal(ens.get(r), s), (L, r)
+            for i, row in enumerate(rows):
+                o = row[r]
+                assert (o.B, o.M, o.Q) == tuple(bmq[i]), (L, r, i)
+                assert np.array_equal(o.R, Ro[i]) and np.array_equal(o.C, Co[i]), (L, r, i)
+            M.append(bmq[-1, 1])
+            R.append(Ro[-1])
+            C.append(Co[-1])
+        # ensemble-mean xi_2 over this size's oracle-checked replicas
+        idx = pick[L]
+        want = orc.xi2(M[-len(idx):], np.array(R[-len(idx):]), np.array(C[-len(idx):]))
+        got = isg.xi2([rows[-1][r].M for r in idx], np.array([rows[-1][r].R for r in idx]),
+                      np.array([rows[-1][r].C for r in idx]))
+        assert (np.isnan(got) and np.isnan(want)) or got == want
+    for L in (512, 1024):
+        for r in pick[L]:
+            lat = isg.Lattice(L, wl.ISING, seed=seeds[r], record_capacity=SWEEPS // EVERY + 1)
+            lat.init_random()
+            lat.sweep(WARM, beta=wl.BETA_C_ISING)
+            lat.sweep(SWEEPS, beta=wl.BETA_C_ISING, record_every=EVERY)
+            recs = lat.read_records()
+            assert np.array_equal(ens.get(r), lat.get()), (L, r)
+            lat.close()
+            for i, row in enumerate(rows):
+                _same(row[r], recs[i])
+    ens.close()
