@@ -66,6 +66,11 @@ def lib():
         L.oracle_xi2.argtypes = [ctypes.c_int64, ctypes.c_int64, i64p, i32p, i32p]
         L.oracle_xi2.restype = ctypes.c_double
         L.oracle_correlation.argtypes = [i8p, ctypes.c_int64, ctypes.c_int64, i64p, i64p, i64p]
+        L.oracle_sw_threshold.argtypes = [ctypes.c_double]
+        L.oracle_sw_threshold.restype = ctypes.c_uint64
+        L.oracle_swendsen_wang.argtypes = [i8p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64,
+                                           ctypes.c_double, i64p]
+        L.oracle_swendsen_wang.restype = ctypes.c_int64
         L.oracle_correlation.restype = ctypes.c_int
         L.oracle_window_init.argtypes = [i8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64]
@@ -210,3 +215,21 @@ def correlation(s: np.ndarray, r):
     if rc != 0:
         raise ValueError("oracle_correlation rejected its arguments")
     return sx, sy
+
+
+def sw_threshold(beta: float) -> int:
+    """Bond threshold rne(2^32 (1 - exp(-2 beta))) of the Swendsen-Wang step."""
+    return int(lib().oracle_sw_threshold(float(beta)))
+
+
+def swendsen_wang(s: np.ndarray, seed: int, k: int, beta: float):
+    """One Swendsen-Wang iteration of the +-1 sites of ``s`` (in place), the
+    k-th on this lattice.  Returns (labels[L, L] int64, number of clusters)."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous and s.shape[0] == s.shape[1]
+    L = s.shape[0]
+    labels = np.empty((L, L), dtype=np.int64)
+    n = lib().oracle_swendsen_wang(_ptr(s, ctypes.c_int8), L, seed & (2**64 - 1), int(k),
+                                   float(beta), _ptr(labels, ctypes.c_int64))
+    if n < 0:
+        raise ValueError("oracle_swendsen_wang rejected its arguments")
+    return labels, int(n)

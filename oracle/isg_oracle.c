@@ -523,3 +523,100 @@ int oracle_correlation(const int8_t *s, int64_t L, int64_t nr, const int64_t *r,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Swendsen-Wang iteration restricted to the sites with s = +-1 (Appendix B: */
+/* the Blume-Capel equilibrium runs combine Swendsen-Wang cluster updates of */
+/* the +-1 spins with Metropolis sweeps, which change s^2; for Ising every  */
+/* site takes part).                                                         */
+/*                                                                           */
+/* Readings where the paper is silent:                                       */
+/*   - Bond (i, j), j the +x (d = 0) or +y (d = 1) neighbour of site         */
+/*     i = y*L + x, is active iff s_i = s_j != 0 and (uint64)u < thr, with  */
+/*     thr = rne(2^32 p), p = 1 - exp(-2 beta) (J = 1; the energy of an      */
+/*     aligned +-1 pair is 2 below an anti-aligned one) computed as          */
+/*     -expm1(-2 beta), and u the Philox4x32-10 word i & 3 of counter        */
+/*     (lo32(i>>2), hi32(i>>2), k, 4 + d), key (lo32(seed), hi32(seed)),     */
+/*     k = the number of Swendsen-Wang iterations done before on this        */
+/*     lattice.  Counter word 3 >= 4 keeps these draws apart from the        */
+/*     sweep (0, 1) and hot-start (2, 3) draws.                              */
+/*   - A cluster is a connected component of active bonds; its label is its */
+/*     smallest site index r.  It flips (s -> -s on all its sites) iff the   */
+/*     word r & 3 of counter (lo32(r>>2), hi32(r>>2), k, 6) is >= 2^31.     */
+/*   - Sites with s = 0 are never bonded and never flip (label = own index). */
+/* ------------------------------------------------------------------------ */
+
+static int64_t uf_root(int64_t *parent, int64_t i)
+{
+    while (parent[i] != i)
+        i = parent[i];
+    return i;
+}
+
+/* Join the components of a and b: the larger root points to the smaller,  */
+/* so every root is the smallest index of its component.                    */
+static void uf_unite(int64_t *parent, int64_t a, int64_t b)
+{
+    a = uf_root(parent, a);
+    b = uf_root(parent, b);
+    if (a < b)
+        parent[b] = a;
+    else if (b < a)
+        parent[a] = b;
+}
+
+uint64_t oracle_sw_threshold(double beta)
+{
+    return (uint64_t)llrint(ldexp(-expm1(-2.0 * beta), 32));
+}
+
+static uint32_t full_index_word(uint64_t seed, uint64_t i, uint32_t k, uint32_t w3)
+{
+    const uint64_t q = i >> 2;
+    const uint32_t ctr[4] = {(uint32_t)q, (uint32_t)(q >> 32), k, w3};
+    const uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[i & 3u];
+}
+
+/* One iteration on s (L x L, updated in place).  labels (L*L, may be NULL)
+ * receives each site's cluster label.  Returns the number of clusters of
+ * +-1 sites, or -1 on bad arguments.                                        */
+int64_t oracle_swendsen_wang(int8_t *s, int64_t L, uint64_t seed, uint64_t k, double beta,
+                             int64_t *labels)
+{
+    if (!s || L < 2 || !(beta >= 0.0) || k > 0xFFFFFFFFull)
+        return -1;
+    const int64_t N = L * L;
+    const uint64_t thr = oracle_sw_threshold(beta);
+    int64_t *parent = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    if (!parent)
+        return -1;
+    for (int64_t i = 0; i < N; ++i)
+        parent[i] = i;
+    for (int64_t y = 0; y < L; ++y)
+        for (int64_t x = 0; x < L; ++x) {
+            const int64_t i = y * L + x;
+            if (s[i] == 0)
+                continue;
+            const int64_t jx = y * L + up1(x, L), jy = up1(y, L) * L + x;
+            if (s[jx] == s[i] && (uint64_t)full_index_word(seed, (uint64_t)i, (uint32_t)k, 4) < thr)
+                uf_unite(parent, i, jx);
+            if (s[jy] == s[i] && (uint64_t)full_index_word(seed, (uint64_t)i, (uint32_t)k, 5) < thr)
+                uf_unite(parent, i, jy);
+        }
+    int64_t clusters = 0;
+    for (int64_t i = 0; i < N; ++i) {
+        parent[i] = uf_root(parent, i);
+        if (s[i] != 0 && parent[i] == i)
+            ++clusters;
+    }
+    if (labels)
+        memcpy(labels, parent, sizeof(int64_t) * (size_t)N);
+    for (int64_t i = 0; i < N; ++i)
+        if (s[i] != 0 && full_index_word(seed, (uint64_t)parent[i], (uint32_t)k, 6) >= 0x80000000u)
+            s[i] = (int8_t)-s[i];
+    free(parent);
+    return clusters;
+}

@@ -38,6 +38,17 @@ MUTATIONS = {
     "correlation partner off by one": (
         "ax += v * s[y * L + (x + r[k]) % L];", "ax += v * s[y * L + (x + r[k] + 1) % L];",
         ["test_oracle_correlation.py"]),
+    "Swendsen-Wang bonds anti-aligned pairs": (
+        "if (s[jx] == s[i] && (uint64_t)full_index_word(seed, (uint64_t)i, (uint32_t)k, 4) < thr)",
+        "if (s[jx] != 0 && (uint64_t)full_index_word(seed, (uint64_t)i, (uint32_t)k, 4) < thr)",
+        ["test_oracle_swendsen_wang.py"]),
+    "Swendsen-Wang bond probability 1 - exp(-beta)": (
+        "ldexp(-expm1(-2.0 * beta), 32)", "ldexp(-expm1(-1.0 * beta), 32)",
+        ["test_oracle_swendsen_wang.py"]),
+    "Swendsen-Wang coin per site instead of per cluster": (
+        "full_index_word(seed, (uint64_t)parent[i], (uint32_t)k, 6)",
+        "full_index_word(seed, (uint64_t)i, (uint32_t)k, 6)",
+        ["test_oracle_swendsen_wang.py"]),
     "hot-start bias": (
         "s[idx] = (int8_t)(u >= 0x80000000u ? 1 : -1);",
         "s[idx] = (int8_t)(u >= 0x7F000000u ? 1 : -1);",
