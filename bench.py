@@ -220,6 +220,44 @@ def precool_bench(n_rep=4096):
             "seconds": time.perf_counter() - t0}
 
 
+def sw_bench(Ls=(4096, 16384), reps=20):
+    """Swendsen-Wang iteration (Appendix B) on a Blume-Capel lattice at the
+    paper's T_c, and the elementary Monte Carlo step (10 Metropolis sweeps +
+    one Swendsen-Wang iteration).  Algorithmic bytes per site of one
+    iteration: labels written (init), read and written (link, flatten),
+    read (coin), read twice (flip: own label, root's coin) = 24 B, plus the
+    spin planes read twice and written once (0.75 B)."""
+    import torch
+
+    import paper_2503_14688_b300 as P
+
+    beta = 1.0 / wl.T_C_BLUME_CAPEL
+    out = []
+    for L in Ls:
+        lat = P.Lattice(L, wl.BLUME_CAPEL, seed=wl.BASE_SEED + 4100)
+        lat.init_random()
+        lat.emcs(3, beta)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.swendsen_wang(beta, n=reps)
+        sw_s = (time.perf_counter() - t0) / reps
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        lat.sweep(10 * reps, beta=beta)
+        torch.cuda.synchronize()
+        sweep_s = (time.perf_counter() - t0) / (10 * reps)
+        lat.close()
+        n = float(L) * L
+        out.append({"L": L, "sw_ms": 1e3 * sw_s, "metropolis_sweep_ms": 1e3 * sweep_s,
+                    "emcs_ms": 1e3 * (sw_s + 10 * sweep_s),
+                    "sw_sites_per_ns": n / sw_s / 1e9,
+                    "sw_GB_per_s": 24.75 * n / sw_s / 1e9,
+                    "labels_MiB": 4 * n / 2**20})
+    return {"workload": "Blume-Capel at T_c (Delta = 0), hot start + 3 EMCS, then 20 "
+                        "Swendsen-Wang iterations (host-timed, each synchronises) and 200 sweeps",
+            "bytes_per_site": 24.75, "sizes": out}
+
+
 def served_bench(n_req=48, load=0.9, chunk=100, max_active=48):
     """The served stream: requests of the served workload (workloads.py)
     through the continuous-batching server.  First all at once (capacity and
@@ -453,6 +491,8 @@ def run_ours(args, w):
             line["served"] = served_bench(n_req=args.served_requests)
         if not args.no_precool and world == 1:
             line["precool"] = precool_bench()
+        if not args.no_sw and world == 1:
+            line["swendsen_wang"] = sw_bench()
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(w.model, beta, w.delta)
         print(json.dumps(line), flush=True)
@@ -469,6 +509,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ising_large")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sw", action="store_true",
+                    help="skip the Swendsen-Wang sub-object")
     ap.add_argument("--no-precool", action="store_true",
                     help="skip the pre-cooling scan (Eq. (8)) sub-object")
     ap.add_argument("--no-batched", action="store_true",

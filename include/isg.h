@@ -386,6 +386,34 @@ isg_status isg_correlation(isg_lattice *lat, int64_t nr, const int64_t *r, int64
  * F(r), are analysis steps left to the caller. */
 double isg_xi_integral(int64_t n, const double *r, const double *c, double r_cut);
 
+/* Swendsen-Wang iteration of the s = +-1 spins (Appendix B: the Blume-Capel
+ * equilibrium runs alternate Metropolis sweeps, which change s^2, with
+ * Swendsen-Wang cluster updates restricted to s = +-1; for Ising every site
+ * takes part).  Bond (i, j), j the +x (d = 0) or +y (d = 1) neighbour of
+ * site i = y L + x, is active iff s_i = s_j != 0 and u < rne(2^32 (1 -
+ * e^{-2 beta})), u the word i & 3 of Philox4x32-10 with key (lo, hi) of
+ * the lattice seed and counter (lo(i >> 2), hi(i >> 2), k, 4 + d), k the
+ * value of isg_sw_iterations before the call.  A cluster (connected
+ * component of active bonds) flips s -> -s iff the word r & 3 of counter
+ * (lo(r >> 2), hi(r >> 2), k, 6) is >= 2^31, r its smallest site index.
+ * Sites with s = 0 never bond nor flip.  The sweep counter is unchanged.
+ * Needs L <= ISG_SW_MAX_L; allocates L^2 4-byte labels on first use (kept
+ * until destroy).  Errors: INVALID (beta < 0 or not finite, L too large,
+ * 2^32 iterations), OOM, DEVICE_TIMEOUT (a bounded device loop ran out;
+ * not expected).  Synchronises. */
+#define ISG_SW_MAX_L 32768
+isg_status isg_swendsen_wang(isg_lattice *lat, double beta);
+
+/* Cluster labels of the last Swendsen-Wang iteration (before its flips):
+ * out[y*L + x] = smallest site index of the site's cluster (its own index
+ * for s = 0).  out: L*L host int32.  INVALID if no iteration has run.
+ * Synchronises. */
+isg_status isg_sw_labels(isg_lattice *lat, int32_t *out);
+
+/* Swendsen-Wang iterations done on this lattice (reset by the init calls,
+ * kept by isg_save / isg_load). */
+isg_status isg_sw_iterations(const isg_lattice *lat, int64_t *count);
+
 /* Energy per spin (-B + Delta Q) / L^2 of one record. */
 double isg_energy_density(const isg_obs *obs, int64_t L, double delta);
 

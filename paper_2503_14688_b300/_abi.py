@@ -18,6 +18,7 @@ ISG_ERR_DEVICE_TIMEOUT = -4
 ISG_ERR_BUSY = -5
 ISG_ERR_UNSUPPORTED = -6
 ISG_NOALLOC_MAX_L = 1 << 18
+ISG_SW_MAX_L = 32768
 ISG_REQ_QUEUED, ISG_REQ_RUNNING, ISG_REQ_DONE = 0, 1, 2
 ISG_ISING = 0
 ISG_BLUME_CAPEL = 1
@@ -103,6 +104,9 @@ PROTOTYPES = {
     "isg_xi2": (_F64, [_I64, _I64, _I64P, _I32P, _I32P]),
     "isg_correlation": (_I32, [_P, _I64, _I64P, _I64P, _I64P]),
     "isg_xi_integral": (_F64, [_I64, _F64P, _F64P, _F64]),
+    "isg_swendsen_wang": (_I32, [_P, _F64]),
+    "isg_sw_labels": (_I32, [_P, _I32P]),
+    "isg_sw_iterations": (_I32, [_P, _I64P]),
     "isg_energy_density": (_F64, [ctypes.POINTER(isg_obs), _I64, _F64]),
     "isg_last_error": (ctypes.c_char_p, []),
     "isg_ensemble_create": (_I32, [ctypes.POINTER(isg_ensemble_desc), ctypes.POINTER(_P)]),

@@ -21,7 +21,8 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["isg_kernels.cu", "isg_api.cu", "isg_noalloc.cu", "isg_ensemble.cu", "isg_server.cu"]
+CU_SOURCES = ["isg_kernels.cu", "isg_api.cu", "isg_noalloc.cu", "isg_ensemble.cu", "isg_server.cu",
+              "isg_sw.cu"]
 CPP_SOURCES = ["isg_host.cpp"]
 
 

@@ -84,6 +84,8 @@ struct isg_lattice {
     int64_t t;               // sweeps done
     int32_t *d_flag;
     int device;
+    uint32_t *sw_labels = nullptr;  // Swendsen-Wang labels (allocated on first use)
+    int64_t sw_count = 0;           // Swendsen-Wang iterations done
 };
 
 namespace {
@@ -292,6 +294,8 @@ void isg_lattice_destroy(isg_lattice *lat)
         cudaFree(lat->records);
     if (lat->d_flag)
         cudaFree(lat->d_flag);
+    if (lat->sw_labels)
+        cudaFree(lat->sw_labels);
     delete lat;
 }
 
@@ -304,6 +308,7 @@ isg_status isg_lattice_init_random(isg_lattice *lat)
     philox_launch_consts(lat->seed, 0u, 3u, &ph1);
     ISG_CUDA(launch_init_random(planes_of(lat), ph0, ph1, lat->stream), "init launch");
     lat->t = 0;
+    lat->sw_count = 0;
     lat->rec_head = lat->rec_count = 0;
     return ISG_OK;
 }
@@ -317,6 +322,7 @@ isg_status isg_lattice_init_uniform(isg_lattice *lat, int8_t value)
         return fail(ISG_ERR_INVALID, "value %d is not a spin of this model", value);
     ISG_CUDA(launch_init_uniform(planes_of(lat), value, lat->stream), "init launch");
     lat->t = 0;
+    lat->sw_count = 0;
     lat->rec_head = lat->rec_count = 0;
     return ISG_OK;
 }
@@ -503,6 +509,7 @@ isg_status isg_save(isg_lattice *lat, const char *path)
     h.seed = lat->seed;
     h.delta = lat->delta;
     h.sweep = lat->t;
+    h.pad = (uint64_t)lat->sw_count;
     h.plane_bytes = isg_lattice_bytes(lat->model, lat->L);
     ISG_CUDA(cudaStreamSynchronize(lat->stream), "stream sync");
     FILE *f = fopen(path, "wb");
@@ -580,6 +587,7 @@ isg_status isg_load(const char *path, void *stream, int64_t record_capacity, isg
         return fail(ISG_ERR_INVALID, "%s is truncated", path);
     }
     lat->t = h.sweep;
+    lat->sw_count = (int64_t)h.pad;
     *out = lat;
     return ISG_OK;
 }
@@ -643,3 +651,62 @@ double isg_energy_density(const isg_obs *obs, int64_t L, double delta)
 const char *isg_last_error(void) { return g_err; }
 
 }  // extern "C"
+
+isg_status isg_swendsen_wang(isg_lattice *lat, double beta)
+{
+    if (!lat)
+        return fail(ISG_ERR_INVALID, "lattice is NULL");
+    if (!(beta >= 0.0) || !std::isfinite(beta))
+        return fail(ISG_ERR_INVALID, "beta must be finite and >= 0 (got %g)", beta);
+    if (lat->L > ISG_SW_MAX_L)
+        return fail(ISG_ERR_INVALID, "Swendsen-Wang labels need L <= %d (L = %lld)", ISG_SW_MAX_L,
+                    (long long)lat->L);
+    if (lat->sw_count > (int64_t)0xFFFFFFFFLL)
+        return fail(ISG_ERR_INVALID, "Swendsen-Wang iteration count exceeds 2^32");
+    const int64_t n = lat->L * lat->L;
+    if (!lat->sw_labels)
+        ISG_CUDA(cudaMalloc(&lat->sw_labels, sizeof(uint32_t) * (size_t)n), "label allocation");
+    PhiloxLaunch px, py, pc;
+    const uint32_t k = (uint32_t)lat->sw_count;
+    philox_launch_consts(lat->seed, k, 4u, &px);
+    philox_launch_consts(lat->seed, k, 5u, &py);
+    philox_launch_consts(lat->seed, k, 6u, &pc);
+    int32_t bad = 0;
+    cudaError_t e = cudaMemsetAsync(lat->d_flag, 0, sizeof(int32_t), lat->stream);
+    if (e == cudaSuccess)
+        e = launch_swendsen_wang(planes_of(lat), lat->sw_labels, px, py, pc, sw_threshold(beta),
+                                 lat->d_flag, lat->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&bad, lat->d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, lat->stream);
+    if (e == cudaSuccess)
+        e = cudaStreamSynchronize(lat->stream);
+    if (e != cudaSuccess)
+        return cuda_fail(e, "Swendsen-Wang");
+    if (bad)
+        return fail(ISG_ERR_DEVICE_TIMEOUT, "Swendsen-Wang union-find exceeded its bound (%d)", bad);
+    ++lat->sw_count;
+    return ISG_OK;
+}
+
+isg_status isg_sw_labels(isg_lattice *lat, int32_t *out)
+{
+    if (!lat || !out)
+        return fail(ISG_ERR_INVALID, "lattice and out must not be NULL");
+    if (!lat->sw_labels || lat->sw_count == 0)
+        return fail(ISG_ERR_INVALID, "no Swendsen-Wang iteration has run on this lattice");
+    const int64_t n = lat->L * lat->L;
+    ISG_CUDA(cudaMemcpyAsync(out, lat->sw_labels, sizeof(int32_t) * (size_t)n,
+                             cudaMemcpyDeviceToHost, lat->stream), "label copy");
+    ISG_CUDA(cudaStreamSynchronize(lat->stream), "label copy");
+    for (int64_t i = 0; i < n; ++i)
+        out[i] &= 0x7FFFFFFF;
+    return ISG_OK;
+}
+
+isg_status isg_sw_iterations(const isg_lattice *lat, int64_t *count)
+{
+    if (!lat || !count)
+        return fail(ISG_ERR_INVALID, "lattice and count must not be NULL");
+    *count = lat->sw_count;
+    return ISG_OK;
+}

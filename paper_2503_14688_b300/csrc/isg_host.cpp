@@ -177,6 +177,13 @@ double xi2_fp64(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const 
 // Integral coherence length (Appendix C): xi = I2 / I1 with
 // I_n = int_0^{r_cut} r^n C(r) dr, by the trapezoid rule over the sampled
 // distances r[0] < r[1] < ... (those beyond r_cut are ignored).
+uint64_t sw_threshold(double beta)
+{
+    // p = 1 - e^{-2 beta} (J = 1: aligned +-1 neighbours lie 2 below
+    // anti-aligned ones), evaluated as -expm1(-2 beta)
+    return (uint64_t)std::llrint(std::ldexp(-std::expm1(-2.0 * beta), 32));
+}
+
 double xi_integral_fp64(int64_t n, const double *r, const double *c, double r_cut)
 {
     if (n < 2 || !r || !c)

@@ -67,6 +67,8 @@ void ising_thresholds(double beta, IsingThr *out);
 void bc_table(double beta, double delta, BcTable *out);
 double xi2_fp64(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const int32_t *C);
 double xi_integral_fp64(int64_t n, const double *r, const double *c, double r_cut);
+// Swendsen-Wang bond threshold rne(2^32 (1 - e^{-2 beta})), 2^32 = always.
+uint64_t sw_threshold(double beta);
 
 // ---- error reporting shared by the C-ABI files (isg_api.cu) ----
 // Stores a printf-style message for isg_last_error() and returns code.
@@ -75,6 +77,12 @@ int32_t report_error(int32_t code, const char *fmt, ...);
 // ---- kernel launchers (isg_kernels.cu); return the launch error ----
 cudaError_t launch_init_random(const Planes &pl, const PhiloxLaunch &ph0, const PhiloxLaunch &ph1,
                                cudaStream_t st);
+// One Swendsen-Wang iteration (isg_sw.cu): labels lab (L*L uint32), Philox
+// constants of the +x bonds, +y bonds and cluster coins, bond threshold, a
+// device error flag raised when a bounded loop runs out.
+cudaError_t launch_swendsen_wang(const Planes &pl, uint32_t *lab, const PhiloxLaunch &px,
+                                 const PhiloxLaunch &py, const PhiloxLaunch &pc, uint64_t thr,
+                                 int32_t *err, cudaStream_t st);
 cudaError_t launch_init_uniform(const Planes &pl, int value, cudaStream_t st);
 cudaError_t launch_half_sweep(const Planes &pl, int colour, const PhiloxLaunch &ph,
                               const IsingThr &ithr, const BcTable *btab, cudaStream_t st);

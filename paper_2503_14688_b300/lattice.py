@@ -185,6 +185,36 @@ class Lattice:
                                         sx.ctypes.data_as(_abi._I64P), sy.ctypes.data_as(_abi._I64P)))
         return sx, sy
 
+    def swendsen_wang(self, beta: float, n: int = 1):
+        """n Swendsen-Wang iterations of the +-1 spins at beta
+        (isg_swendsen_wang; Appendix B)."""
+        for _ in range(int(n)):
+            check(self._lib.isg_swendsen_wang(self._h, float(beta)))
+
+    def sw_labels(self) -> np.ndarray:
+        """Cluster labels (smallest site index) of the last Swendsen-Wang
+        iteration, (L, L) int32."""
+        out = np.empty((self.L, self.L), dtype=np.int32)
+        check(self._lib.isg_sw_labels(self._h, out.ctypes.data_as(_abi._I32P)))
+        return out
+
+    @property
+    def sw_iterations(self) -> int:
+        c = ctypes.c_int64()
+        check(self._lib.isg_sw_iterations(self._h, ctypes.byref(c)))
+        return c.value
+
+    def emcs(self, n: int, beta: float, sweeps: int = 10, record_every: int = 0):
+        """n elementary Monte Carlo steps of Appendix B: `sweeps` Metropolis
+        sweeps then one Swendsen-Wang iteration; with record_every = k > 0
+        the observables are recorded after every k-th step."""
+        for i in range(1, int(n) + 1):
+            if sweeps:
+                self.sweep(sweeps, beta=beta)
+            self.swendsen_wang(beta)
+            if record_every and i % record_every == 0:
+                self.record()
+
     def measure(self) -> Obs:
         R = np.zeros(self.L, dtype=np.int32)
         C = np.zeros(self.L, dtype=np.int32)
