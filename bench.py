@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Throughput of the checkerboard Metropolis sweep on one B300 (or N replicas).
 
-A step is one pass of the whole hot path over the workload: the host
-threshold table for beta(t), the colour-0 and colour-1 half-sweeps, and the
-observables (B, M, Q, row and column sums) recorded on the device.  The
-default workload is the single large Ising lattice, L = 2^20 (2^40 spins,
-128 GiB of bit-planes), hot start, quench to beta_c; the lattice is far larger
-than L2, so no flush is needed between steps.
+A step is one sweep of the whole hot path over the workload: the host
+threshold table for beta(t), the colour-0 and colour-1 half-sweeps, and, at
+the workload's cadence, the observables (B, M, Q, row and column sums)
+recorded on the device -- every 10 sweeps for the large quench (its xi(t) is
+logged every 10 sweeps), every sweep for the small workloads; the line also
+reports the step recording every sweep.  The default workload is the single
+large Ising lattice, L = 2^20 (2^40 spins, 128 GiB of bit-planes), hot start,
+quench to beta_c; the lattice is far larger than L2, so no flush is needed
+between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload ising_large|blume_capel_large|ising_small|blume_capel_parity]
@@ -379,8 +382,12 @@ def run_ours(args, w):
                     record_capacity=args.steps + args.warmup + 4)
     lat.init_random()
     beta = w.beta
+    # observables (B, M, Q, R, C) recorded on the device at the workload's
+    # cadence: every 10 sweeps for the large quench ("xi(t) growth logged
+    # every 10 sweeps"), every sweep for the small ones
+    every = max(1, int(w.record_every))
 
-    def step(events=None):
+    def step(i, events=None, record_every=every):
         if events is not None:
             events[0].record(stream)
         lat.half_sweep(0, beta)
@@ -389,10 +396,11 @@ def run_ours(args, w):
         lat.half_sweep(1, beta)
         if events is not None:
             events[2].record(stream)
-        lat.record()
+        if (i + 1) % record_every == 0:
+            lat.record()
 
-    for _ in range(args.warmup):
-        step()
+    for i in range(args.warmup):
+        step(i)
     lat.read_records(with_sums=False)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -403,7 +411,7 @@ def run_ours(args, w):
     clocks.start()
     start.record(stream)
     for i in range(args.steps):
-        step(evs[i])
+        step(i, evs[i])
     stop.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -413,16 +421,31 @@ def run_ours(args, w):
     half0 = [e[0].elapsed_time(e[1]) for e in evs]
     half1 = [e[1].elapsed_time(e[2]) for e in evs]
     recs = lat.read_records()
-    assert len(recs) == args.steps
-    xi = P.xi2([recs[-1].M], recs[-1].R[None], recs[-1].C[None])
+    assert len(recs) == args.steps // every
+    xi = P.xi2([recs[-1].M], recs[-1].R[None], recs[-1].C[None]) if recs else None
+
+    # the same step recording every sweep, for comparison (5 steps)
+    n_each = min(args.steps, 5)
+    a_ev, b_ev = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a_ev.record(stream)
+    for i in range(n_each):
+        step(i, record_every=1)
+    b_ev.record(stream)
+    torch.cuda.synchronize()
+    ms_each = a_ev.elapsed_time(b_ev) / n_each
+    lat.read_records(with_sums=False)
 
     # end to end through the C ABI: host beta in, host record out, xi_2 on host
-    e2e_steps = max(2, min(args.steps, 5))
-    betas_host = np.full(1, beta)
+    # (per call: `every` sweeps with their betas from a host array, the
+    # record read back to host arrays)
+    e2e_calls = max(1, min(args.steps // every, 2)) if every > 1 else max(2, min(args.steps, 5))
+    e2e_steps = e2e_calls * every
+    betas_host = np.full(every, beta)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        lat.sweep(1, betas=betas_host, record_every=1)
+    for _ in range(e2e_calls):
+        lat.sweep(every, betas=betas_host, record_every=every)
         r = lat.read_records()[0]
         P.xi2([r.M], r.R[None], r.C[None])
     e2e_s = time.perf_counter() - t0
@@ -440,6 +463,7 @@ def run_ours(args, w):
     ms, e2e_s = replicas.max_over_ranks([ms, e2e_s], device="cuda")
     sites = float(w.L) * float(w.L)
     value = replicas.weak_scaling_value(world, sites, args.steps, ms)
+    weak_each = replicas.weak_scaling_value(world, sites, 1, ms_each)
     e2e_value = replicas.weak_scaling_value(world, sites, e2e_steps, e2e_s * 1e3)
 
     sm_max, peak_src = _peaks()
@@ -459,8 +483,10 @@ def run_ours(args, w):
                        "L": w.L, "spins": int(sites), "beta": beta, "delta": w.delta,
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2_flush": _l2_note(P.Lattice.nbytes(w.model, w.L)),
-                       "step": "host thresholds + half-sweep colour 0 + half-sweep colour 1 "
-                               "+ on-device record of B, M, Q, row and column sums"},
+                       "step": "host thresholds + half-sweep colour 0 + half-sweep colour 1; "
+                               "every record_every steps an on-device record of B, M, Q, "
+                               "row and column sums",
+                       "record_every": every},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                          "frac": achieved / peak,
                          "traffic": DRAM_BYTES_PER_SITE[w.model] * sites / 2,
@@ -480,8 +506,10 @@ def run_ours(args, w):
                              "achieved_sites_per_ns": sites / 2 / (dom_ms * 1e6),
                              "frac": sites / 2 / (dom_ms * 1e6) / wide_bound}},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8,
-                    "d2h_bytes_per_step": 32 + 8 * w.L, "steps": e2e_steps},
-            "gpu_launches": 3 * args.steps,
+                    "d2h_bytes_per_step": (32 + 8 * w.L) / every, "steps": e2e_steps},
+            "gpu_launches": 2 * args.steps + args.steps // every,
+            "record_every_sweep": {"ms_per_step": ms_each,
+                                   "value": weak_each, "unit": UNIT, "steps": n_each},
             "clocks": clk,
             "xi2_last": xi,
             "correlation": corr,
