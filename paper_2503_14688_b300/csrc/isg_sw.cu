@@ -115,12 +115,12 @@ __device__ __forceinline__ bool unite(uint32_t *lab, uint32_t a, uint32_t b)
     return false;
 }
 
-// --- pass 1: union-find inside 32 x 32 tiles, in shared memory ----------
-// A block owns one tile; thread t handles sites 4 (t & 7) .. +3 of tile row
-// t >> 3.  Bonds whose both ends lie in the tile are joined here; local
-// indices ty * 32 + tx are ordered like the global ones, so each local root
-// is the smallest global index of its local component.  Every site's label
-// becomes the global index of its local root (roots keep their own index).
+// --- pass 1: union-find inside 32 x kTileH tiles, in shared memory -------
+// A block owns one tile, one thread per site (warp = tile row).  Bonds whose
+// both ends lie in the tile are joined here; local indices ty * 32 + tx are
+// ordered like the global ones, so each local root is the smallest global
+// index of its local component.  Every site's label becomes the global index
+// of its local root (roots keep their own index).
 constexpr int kTile = 32;   // tile width (one warp per tile row)
 #ifndef ISG_SW_TILE_H
 #define ISG_SW_TILE_H 16
