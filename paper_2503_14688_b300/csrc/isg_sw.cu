@@ -14,19 +14,20 @@
 //
 // GPU layout: one uint32 label per site (row-major, L <= 2^15 so labels fit
 // 30 bits; bit 31 carries a root's coin after pass 3).  Passes:
-//   1. k_sw_local:    one block per 32 x 16 tile, one thread per site.  A
-//                     lane computes each Philox call and shares its words by
-//                     shuffle.  Horizontal runs come from a warp ballot of
-//                     the +x bonds (a site's run starts one past the last
-//                     unbonded position to its left).  Vertical bonds join
-//                     runs by a lock-free union-find in shared memory whose
-//                     links always point from the larger root to the
-//                     smaller (atomicMin), row boundaries in stages (bands
-//                     of 1, 2, 4, 8 rows merged pairwise).  Each label
-//                     becomes the global index of its local root.  (Tile
-//                     height 16: 11.9 ms per iteration at L = 16384 against
-//                     12.9 ms for 32 x 32 tiles, which leave fewer blocks
-//                     resident per SM to hide the passes' latencies.)
+//   1. k_sw_local_w:  one warp per 32 x 32 tile (four tiles per block).
+//                     The warp first loads the tile's spins into shared
+//                     memory, then walks its rows in order: a lane computes
+//                     each Philox call and shares its words by shuffle; the
+//                     row's horizontal runs come from a ballot of its +x
+//                     bonds (a site's run starts one past the last unbonded
+//                     position to its left); the vertical bonds to the row
+//                     above join runs by a lock-free union-find in shared
+//                     memory whose links always point from the larger root
+//                     to the smaller (atomicMin).  Each label becomes the
+//                     global index of its local root.  (Against one block
+//                     per tile with all rows at once: 7.0 vs 11.9 ms per
+//                     iteration at L = 16384 -- no block barriers, shallow
+//                     trees, 64 tiles in flight per SM instead of 4.)
 //   2. k_sw_boundary: bonds crossing a tile edge, joined the same way in
 //                     global memory.  Every final root is the smallest index
 //                     of its component whatever the execution order: the
@@ -116,18 +117,16 @@ __device__ __forceinline__ bool unite(uint32_t *lab, uint32_t a, uint32_t b)
 }
 
 // --- pass 1: union-find inside 32 x kTileH tiles, in shared memory -------
-// A block owns one tile, one thread per site (warp = tile row).  Bonds whose
-// both ends lie in the tile are joined here; local indices ty * 32 + tx are
-// ordered like the global ones, so each local root is the smallest global
-// index of its local component.  Every site's label becomes the global index
-// of its local root (roots keep their own index).
+// Bonds whose both ends lie in a tile are joined here; local indices
+// r * 32 + tx are ordered like the global ones, so each local root is the
+// smallest global index of its local component.  Every site's label becomes
+// the global index of its local root (roots keep their own index).
 constexpr int kTile = 32;   // tile width (one warp per tile row)
 #ifndef ISG_SW_TILE_H
-#define ISG_SW_TILE_H 16
+#define ISG_SW_TILE_H 32
 #endif
-constexpr int kTileH = ISG_SW_TILE_H;  // tile height (rows = warps per block)
-constexpr int kStages = kTileH == 32 ? 5 : kTileH == 16 ? 4 : kTileH == 8 ? 3 : 2;
-static_assert(kTileH == 32 || kTileH == 16 || kTileH == 8 || kTileH == 4, "tile height");
+constexpr int kTileH = ISG_SW_TILE_H;  // tile height (rows walked by one warp)
+static_assert(kTileH >= 2 && kTileH <= 32, "tile height");
 
 __device__ __forceinline__ uint32_t find_local(volatile uint32_t *ls, uint32_t i, int &budget)
 {
@@ -167,79 +166,89 @@ __device__ __forceinline__ bool unite_local(uint32_t *ls, uint32_t a, uint32_t b
     return false;
 }
 
-__global__ void __launch_bounds__(32 * kTileH) k_sw_local(Planes pl, uint32_t *lab, PhiloxLaunch px,
-                                                    PhiloxLaunch py, uint32_t thr, int full,
-                                                    int32_t *err)
+// One warp per 32 x kTileH tile, rows walked in order (see pass 1 above).
+constexpr int kWarpsPerBlock = 4;
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) k_sw_local_w(Planes pl, uint32_t *lab,
+                                                                   PhiloxLaunch px, PhiloxLaunch py,
+                                                                   uint32_t thr, int full,
+                                                                   int32_t *err)
 {
-    // one thread per site: warp ty = tile row, lane tx = tile column
-    __shared__ int8_t s_spin[kTileH][kTile];
-    __shared__ uint32_t s_lab[kTileH * kTile];
-    __shared__ uint32_t s_hm[kTileH];  // per row: bit tx = bond from tx to tx + 1
+    __shared__ uint32_t s_all[kWarpsPerBlock][kTileH * kTile];
+    __shared__ int8_t s_sp[kWarpsPerBlock][kTileH][kTile];
+    const int wid = threadIdx.x >> 5, tx = threadIdx.x & 31;
     const int64_t L = pl.L;
-    const int tiles_x = (int)(L / kTile);
-    const int bx = (int)(blockIdx.x % tiles_x), by = (int)(blockIdx.x / tiles_x);
-    const int ty = threadIdx.x >> 5, tx = threadIdx.x & 31;
-    const int64_t y = (int64_t)by * kTileH + ty, x = (int64_t)bx * kTile + tx;
-    const int sv = spin_at(pl, x, y);
-    s_spin[ty][tx] = (int8_t)sv;
-    // bond words: lane 4a computes the +x call and lane 4a + 1 the +y call of
-    // the four sites 4a .. 4a+3; every lane then fetches its own two words
-    const int64_t g = (y * L + (int64_t)bx * kTile + (tx & ~3)) >> 2;
-    uint32_t w[4] = {0u, 0u, 0u, 0u};
-    if ((tx & 3) < 2) {
-        const PhiloxLaunch &pc = (tx & 1) ? py : px;
-        philox_site4(pc, philox_word_part(pc, (uint32_t)((uint64_t)g >> 32)), (uint32_t)g, w[0],
-                     w[1], w[2], w[3]);
-    }
-    const int src = tx & ~3;
-    uint32_t ux = 0, uy = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint32_t a = __shfl_sync(0xFFFFFFFFu, w[k], src);
-        const uint32_t b = __shfl_sync(0xFFFFFFFFu, w[k], src + 1);
-        if ((tx & 3) == k) {
-            ux = a;
-            uy = b;
-        }
-    }
-    __syncthreads();
-    const bool hb = tx + 1 < kTile && sv != 0 && s_spin[ty][tx + 1] == sv && (full || ux < thr);
-    const bool vb = ty + 1 < kTileH && sv != 0 && s_spin[ty + 1][tx] == sv && (full || uy < thr);
-    const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hb);
-    const uint32_t vm = __ballot_sync(0xFFFFFFFFu, vb);
-    // horizontal run: its first site is one past the last position below tx
-    // without a bond to its right (or 0)
-    const uint32_t z = ~hm & ((1u << tx) - 1u);
-    const int start = z ? 32 - __clz(z) : 0;
-    s_lab[ty * kTile + tx] = (uint32_t)(ty * kTile + start);
-    if (tx == 0)
-        s_hm[ty] = hm;
-    __syncthreads();
-    // vertical bonds join runs; a bond whose left neighbour also has one,
-    // with both rows' runs continuing across, joins the same two runs: skip.
-    // The boundary below row ty is joined at stage ctz(ty + 1): bands of 2,
-    // 4, 8, 16 rows are merged pairwise, so the trees stay shallow and few
-    // rows contend at a time.
+    const int64_t tiles_x = L / kTile, n_tiles = tiles_x * (L / kTileH);
+    const int64_t tile = (int64_t)blockIdx.x * kWarpsPerBlock + wid;
+    if (tile >= n_tiles)
+        return;  // whole warp
+    const int64_t bx = tile % tiles_x, by = tile / tiles_x;
+    uint32_t *sl = s_all[wid];
+    const int64_t x = bx * kTile + tx;
     bool ok = true;
-    const bool dup = tx > 0 && ((vm >> (tx - 1)) & 1u) && ((hm >> (tx - 1)) & 1u) &&
-                     ((s_hm[ty + 1 < kTileH ? ty + 1 : ty] >> (tx - 1)) & 1u);
-    const int stage = __ffs(ty + 1) - 1;
+    int s_prev = 0;
+    uint32_t uy_prev = 0, hm_prev = 0;
+    const PhiloxLaunch &pc = (tx & 1) ? py : px;
+    // all spins of the tile first: independent loads, issued together
+#pragma unroll 8
+    for (int r = 0; r < kTileH; ++r)
+        s_sp[wid][r][tx] = (int8_t)spin_at(pl, x, by * kTileH + r);
+    __syncwarp();
 #pragma unroll 1
-    for (int k = 0; k < kStages; ++k) {
-        if (vb && !dup && stage == k)
-            ok &= unite_local(s_lab, (uint32_t)(ty * kTile + tx), (uint32_t)((ty + 1) * kTile + tx));
-        __syncthreads();
+    for (int r = 0; r < kTileH; ++r) {
+        const int64_t y = by * kTileH + r;
+        const int sv = s_sp[wid][r][tx];
+        const int64_t g = (y * L + bx * kTile + (tx & ~3)) >> 2;
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if ((tx & 3) < 2)
+            philox_site4(pc, philox_word_part(pc, (uint32_t)((uint64_t)g >> 32)), (uint32_t)g, w[0],
+                         w[1], w[2], w[3]);
+        const int src = tx & ~3;
+        uint32_t ux = 0, uy = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const uint32_t a = __shfl_sync(0xFFFFFFFFu, w[k], src);
+            const uint32_t b = __shfl_sync(0xFFFFFFFFu, w[k], src + 1);
+            if ((tx & 3) == k) {
+                ux = a;
+                uy = b;
+            }
+        }
+        const int sr = __shfl_down_sync(0xFFFFFFFFu, sv, 1);
+        const bool hb = tx + 1 < kTile && sv != 0 && sr == sv && (full || ux < thr);
+        const uint32_t hm = __ballot_sync(0xFFFFFFFFu, hb);
+        const uint32_t z = ~hm & ((1u << tx) - 1u);
+        const int start = z ? 32 - __clz(z) : 0;
+        sl[r * kTile + tx] = (uint32_t)(r * kTile + start);
+        __syncwarp();
+        if (r > 0) {
+            const bool vb = s_prev != 0 && s_prev == sv && (full || uy_prev < thr);
+            const uint32_t vm = __ballot_sync(0xFFFFFFFFu, vb);
+            const bool dup = tx > 0 && ((vm >> (tx - 1)) & 1u) && ((hm_prev >> (tx - 1)) & 1u) &&
+                             ((hm >> (tx - 1)) & 1u);
+            if (vb && !dup)
+                ok &= unite_local(sl, (uint32_t)((r - 1) * kTile + tx), (uint32_t)(r * kTile + tx));
+            __syncwarp();
+        }
+        s_prev = sv;
+        uy_prev = uy;
+        hm_prev = hm;
     }
-    int budget = kFindBudget;
-    uint32_t r = (uint32_t)(ty * kTile + tx);
-    while (budget-- > 0) {  // read-only walk: labels are final in shared memory
-        const uint32_t p = s_lab[r];
-        if (p == r)
-            break;
-        r = p;
+    __syncwarp();
+#pragma unroll 1
+    for (int r = 0; r < kTileH; ++r) {
+        int budget = kFindBudget;
+        uint32_t q = (uint32_t)(r * kTile + tx);
+        while (budget-- > 0) {
+            const uint32_t p = sl[q];
+            if (p == q)
+                break;
+            q = p;
+        }
+        ok &= budget > 0;
+        const int64_t y = by * kTileH + r;
+        lab[y * L + x] = (uint32_t)((by * kTileH + (q >> 5)) * L + bx * kTile + (q & 31));
     }
-    ok &= budget > 0;
-    lab[y * L + x] = (uint32_t)(((int64_t)by * kTileH + (r >> 5)) * L + (int64_t)bx * kTile + (r & 31));
     if (!ok)
         atomicOr(err, 1);
 }
@@ -390,7 +399,8 @@ cudaError_t launch_swendsen_wang(const Planes &pl, uint32_t *lab, const PhiloxLa
     const int th = 256;
     const int full = thr >= (1ull << 32) ? 1 : 0;
     const int64_t tiles = (pl.L / kTile) * (pl.L / kTileH);
-    k_sw_local<<<(unsigned)tiles, 32 * kTileH, 0, st>>>(pl, lab, px, py, (uint32_t)thr, full, err);
+    k_sw_local_w<<<(unsigned)((tiles + kWarpsPerBlock - 1) / kWarpsPerBlock), 32 * kWarpsPerBlock, 0,
+                   st>>>(pl, lab, px, py, (uint32_t)thr, full, err);
     k_sw_boundary<<<grid_for(tiles * (kTileH + 8), th), th, 0, st>>>(pl, lab, px, py,
                                                                       (uint32_t)thr, full, err);
     k_sw_resolve<<<grid_for(n / 4, th), th, 0, st>>>(lab, n, pc, err);
