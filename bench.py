@@ -142,12 +142,13 @@ def cpu_baseline(model, beta, delta, budget_s=12.0, seed=wl.BASE_SEED + 99):
     threads = oracle.default_threads()
     L = 4096
     s = oracle.init_random(L, model, seed)
+    oracle.run(s, model, seed, 0, [beta], delta=delta, nthreads=threads)  # warm-up (threads, pages)
     t0 = time.perf_counter()
-    oracle.run(s, model, seed, 0, [beta], delta=delta, nthreads=threads)
-    one = time.perf_counter() - t0
-    n = max(1, min(2000, int(budget_s / max(one, 1e-6))))
+    oracle.run(s, model, seed, 1, [beta] * 3, delta=delta, nthreads=threads)
+    one = (time.perf_counter() - t0) / 3
+    n = max(1, min(4000, int(budget_s / max(one, 1e-6))))
     t0 = time.perf_counter()
-    oracle.run(s, model, seed, 1, [beta] * n, delta=delta, record_every=n, nthreads=threads)
+    oracle.run(s, model, seed, 4, [beta] * n, delta=delta, record_every=n, nthreads=threads)
     dt = time.perf_counter() - t0
     return {"value": L * L * n / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{'Ising' if model == 0 else 'Blume-Capel'} L={L} hot start, {n} sweeps "
