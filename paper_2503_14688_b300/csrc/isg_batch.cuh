@@ -66,7 +66,7 @@ struct EnsArgs {
 size_t smem_bytes_for(int32_t model, int64_t L)
 {
     const size_t planes = (size_t)L * (size_t)L / (model == ISG_ISING ? 8 : 4);
-    const size_t spread = model == ISG_ISING ? 0 : sizeof(uint2) * kBcSpread * 256;
+    const size_t spread = model == ISG_ISING ? 0 : sizeof(uint32_t) * kBcSpread * kBcNibbleTable;
     return planes + 8 * (size_t)L + 4 * kBcTableSize + 64 + spread;
 }
 
@@ -204,6 +204,40 @@ __device__ void smem_measure(const uint32_t *P, int L, int W, int32_t *R_s, int3
     __syncthreads();
 }
 
+// One Blume-Capel colour of a replica held in shared memory; the threads
+// walk its words from (y, w) in steps of (dy, dw).
+template <bool kFull>
+__device__ __forceinline__ void bc_smem_colour(uint32_t *P, int L, int W, int c, int y, int w,
+                                               int dy, int dw, uint64_t qrow,
+                                               const PhiloxLaunch &pc, const uint32_t *s_thr,
+                                               const uint32_t *s_nib)
+{
+    const int LW = L * W;
+    const uint32_t *nbn = P + 2 * (1 - c) * LW, *nbp = nbn + LW;
+    uint32_t *tn = P + 2 * c * LW, *tp = tn + LW;
+    while (y < L) {
+        const int yu = y == 0 ? L - 1 : y - 1, yd = y + 1 == L ? 0 : y + 1;
+        const int par = (c ^ y) & 1;
+        const int ew = par == 0 ? (w == 0 ? W - 1 : w - 1) : (w + 1 == W ? 0 : w + 1);
+        const uint32_t sn = nbn[y * W + w], sp = nbp[y * W + w];
+        const uint32_t nn[4] = {nbn[yu * W + w], nbn[yd * W + w], sn,
+                                side_word(sn, nbn[y * W + ew], par)};
+        const uint32_t pp[4] = {nbp[yu * W + w], nbp[yd * W + w], sp,
+                                side_word(sp, nbp[y * W + ew], par)};
+        uint32_t n = tn[y * W + w], p = tp[y * W + w];
+        const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)w;
+        bc_word_update<kFull>(n, p, nn, pp, q0, pc, s_thr, s_nib);
+        tn[y * W + w] = n;
+        tp[y * W + w] = p;
+        w += dw;
+        y += dy;
+        if (w >= W) {
+            w -= W;
+            ++y;
+        }
+    }
+}
+
 template <int MODEL>
 __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
 {
@@ -215,14 +249,14 @@ __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
     int32_t *C_s = R_s + L;
     uint32_t *s_thr = reinterpret_cast<uint32_t *>(C_s + L);
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(s_thr + kBcTableSize);
-    uint2 *s_spread = reinterpret_cast<uint2 *>(acc + 4);  // Blume-Capel only
+    uint32_t *s_nib = reinterpret_cast<uint32_t *>(acc + 4);  // Blume-Capel only
 
     const uint4 *g4 = reinterpret_cast<const uint4 *>(it.planes);
     uint4 *s4 = reinterpret_cast<uint4 *>(P);
     for (int i = tid; i < nplanes * LW / 4; i += nt)
         s4[i] = g4[i];
     if (MODEL == 1)
-        bc_spread_fill(s_spread, tid, nt);
+        bc_spread_fill(s_nib, tid, nt);
     __syncthreads();
 
     const int dy = nt / W, dw = nt - (nt / W) * W;
@@ -238,9 +272,11 @@ __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
     const int rec_row0 = it.own ? it.rec_row0 : a.rec_row0;
     for (int s = 0; s < nsweeps; ++s) {
         const uint32_t t = t0 + (uint32_t)s;
+        bool bc_full = false;
         if (MODEL == 1) {
             for (int i = tid; i < kBcTableSize; i += nt)
                 s_thr[i] = btab[s].thr[i];
+            bc_full = btab[s].full != 0;
             __syncthreads();
         }
         for (int c = 0; c < 2; ++c) {
@@ -266,30 +302,10 @@ __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
                         ++y;
                     }
                 }
+            } else if (bc_full) {
+                bc_smem_colour<true>(P, L, W, c, y, w, dy, dw, qrow, pc, s_thr, s_nib);
             } else {
-                const uint32_t *nbn = P + 2 * (1 - c) * LW, *nbp = nbn + LW;
-                uint32_t *tn = P + 2 * c * LW, *tp = tn + LW;
-                while (y < L) {
-                    const int yu = y == 0 ? L - 1 : y - 1, yd = y + 1 == L ? 0 : y + 1;
-                    const int par = (c ^ y) & 1;
-                    const int ew = par == 0 ? (w == 0 ? W - 1 : w - 1) : (w + 1 == W ? 0 : w + 1);
-                    const uint32_t sn = nbn[y * W + w], sp = nbp[y * W + w];
-                    const uint32_t nn[4] = {nbn[yu * W + w], nbn[yd * W + w], sn,
-                                            side_word(sn, nbn[y * W + ew], par)};
-                    const uint32_t pp[4] = {nbp[yu * W + w], nbp[yd * W + w], sp,
-                                            side_word(sp, nbp[y * W + ew], par)};
-                    uint32_t n = tn[y * W + w], p = tp[y * W + w];
-                    const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)w;
-                    bc_word_update(n, p, nn, pp, q0, pc, s_thr, s_spread);
-                    tn[y * W + w] = n;
-                    tp[y * W + w] = p;
-                    w += dw;
-                    y += dy;
-                    if (w >= W) {
-                        w -= W;
-                        ++y;
-                    }
-                }
+                bc_smem_colour<false>(P, L, W, c, y, w, dy, dw, qrow, pc, s_thr, s_nib);
             }
             __syncthreads();
         }

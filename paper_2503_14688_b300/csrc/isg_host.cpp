@@ -63,6 +63,7 @@ void bc_table(double beta, double delta, BcTable *out)
     const uint32_t always = 0x80000000u;  // (u >> 1) < 2^31 for every u
     for (int i = 0; i < kBcTableSize; ++i)
         out->thr[i] = always;
+    uint32_t lowest = always;
     for (int s = -1; s <= 1; ++s) {
         const int n = s != 0, p = s > 0;
         for (int b = 0; b < 2; ++b) {
@@ -74,10 +75,16 @@ void bc_table(double beta, double delta, BcTable *out)
                 uint32_t thr = always;
                 if (dE > 0.0)
                     thr = (uint32_t)grid_threshold(beta, dE, 31);
-                out->thr[(b << 6) | (n << 5) | (p << 4) | g] = thr;
+                out->thr[bc_entry(n, p, b, g)] = thr;
+                lowest = thr < lowest ? thr : lowest;
             }
         }
     }
+    // v < thr31  <=>  u = 2 v + b <= 2 thr31 - 1, representable unless thr31 = 0
+    out->full = lowest >= 1u;
+    if (out->full)
+        for (int i = 0; i < kBcTableSize; ++i)
+            out->thr[i] = 2u * out->thr[i] - 1u;
 }
 
 // ---------------------------------------------------------------------------

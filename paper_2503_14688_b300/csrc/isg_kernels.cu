@@ -234,20 +234,20 @@ __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
 // Blume-Capel half-sweep.  Two bit-planes per colour: n (s != 0) and p (s > 0).
 // The neighbour field h + 4 = #(+1 neighbours) + #(neighbours != -1) is a
 // bit-sliced sum of eight indicator words (four bits g0..g3); each site
-// then looks its threshold up in a 128-entry table indexed by
-// (n, p, proposal bit, h + 4) held in shared memory.
+// then looks its threshold up in the table of BcTable, indexed by
+// (proposal bit, n + p, h + 4) and held in shared memory.
 // ---------------------------------------------------------------------------
-template <int V>
+template <int V, bool kFull>
 __global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
     k_bc_half(uint32_t *__restrict__ tn_plane, uint32_t *__restrict__ tp_plane,
               const uint32_t *__restrict__ nn_plane, const uint32_t *__restrict__ np_plane,
               int64_t L, int64_t W, int colour, int H, PhiloxLaunch pc, BcTable tab)
 {
     __shared__ uint32_t s_thr[kBcTableSize];
-    __shared__ uint2 s_spread[kBcSpread * 256];
+    __shared__ uint32_t s_nib[kBcSpread * kBcNibbleTable];
     for (int i = threadIdx.x; i < kBcTableSize; i += blockDim.x)
         s_thr[i] = tab.thr[i];
-    bc_spread_fill(s_spread, threadIdx.x, blockDim.x);
+    bc_spread_fill(s_nib, threadIdx.x, blockDim.x);
     __syncthreads();
 
     const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -280,7 +280,7 @@ __global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
             const uint32_t nbn[4] = {Un.v[v], Dn.v[v], Sn.v[v], Xn.v[v]};
             const uint32_t nbp[4] = {Up.v[v], Dp.v[v], Sp.v[v], Xp.v[v]};
             const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)(w0 + v);
-            bc_word_update(Tn.v[v], Tp.v[v], nbn, nbp, q0, pc, s_thr, s_spread);
+            bc_word_update<kFull>(Tn.v[v], Tp.v[v], nbn, nbp, q0, pc, s_thr, s_nib);
         }
         store_words<V>(tn_plane + y * W + w0, Tn);
         store_words<V>(tp_plane + y * W + w0, Tp);
@@ -729,8 +729,11 @@ cudaError_t launch_bc(const Planes &pl, int colour, const PhiloxLaunch &ph, cons
     const int64_t tpr = pl.W / V;
     const int H = sweep_band(pl.L, tpr, kBcMinBlocks, kBcThreads, 2);
     const int64_t threads = tpr * ((pl.L + H - 1) / H);
-    k_bc_half<V><<<(unsigned)((threads + kBcThreads - 1) / kBcThreads), kBcThreads, 0, st>>>(
-        tn, tp, nn, np, pl.L, pl.W, colour, H, ph, tab);
+    const unsigned blocks = (unsigned)((threads + kBcThreads - 1) / kBcThreads);
+    if (tab.full)
+        k_bc_half<V, true><<<blocks, kBcThreads, 0, st>>>(tn, tp, nn, np, pl.L, pl.W, colour, H, ph, tab);
+    else
+        k_bc_half<V, false><<<blocks, kBcThreads, 0, st>>>(tn, tp, nn, np, pl.L, pl.W, colour, H, ph, tab);
     return cudaGetLastError();
 }
 

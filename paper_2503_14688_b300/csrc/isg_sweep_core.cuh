@@ -96,41 +96,45 @@ __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uin
     cy = (a & b) | (c & (a ^ b));
 }
 
-// Blume-Capel per-site threshold lookup.  The table index of a site is
-// (b << 6) | (n << 5) | (p << 4) | g with b its proposal bit (u & 1), n, p its
-// bit-planes and g = h + 4; as a byte offset into the 128-entry u32 table:
-// (b << 8) | (idx6 << 2), idx6 = (n << 5) | (p << 4) | g.
+// Blume-Capel per-site threshold lookup.  A site's table entry is
+// g + 9 (n + p) + 64 b (BcTable); as a byte offset into the u32 table,
+// 4 (g + 9 (n + p)) + 256 b.
 //
-// The six planes g0..g3, p, n are known before the random numbers; their
-// bits are spread to one byte per site with 256-entry lookup tables in
-// shared memory: kBcSpread tables (one per plane k), entry v holding, in
-// byte m of a 64-bit word, bit k + 2 equal to bit m of v.  OR-ing the six
-// entries of a byte of each plane gives the scaled index of 8 sites at once.
+// The six planes g0..g3, p, n are known before the random numbers.  Their
+// bits are turned into one byte per site, 4 (g + 9 (n + p)) <= 104, four
+// sites at a time: each plane's nibble of the four sites indexes a 16-entry
+// table (kBcSpread tables in shared memory, one per plane) whose entry holds
+// the plane's weight (4, 8, 16, 32 for g0..g3, 36 for p and n) in the byte of
+// every site whose bit is set; the six entries are added.  Sixteen-entry
+// tables span half the shared-memory banks, so the 32 lanes of a warp never
+// conflict on them.  Per site, one byte permute then joins the index byte
+// with the proposal bit b = u & 1 at bit 8.
 constexpr int kBcSpread = 6;
+constexpr int kBcNibbleTable = 16;
 
-__device__ __forceinline__ void bc_spread_fill(uint2 *s_spread, int tid, int nt)
+__device__ __forceinline__ void bc_spread_fill(uint32_t *s_nib, int tid, int nt)
 {
-    for (int i = tid; i < kBcSpread * 256; i += nt) {
-        const int k = i >> 8, v = i & 255;
-        uint32_t lo = 0, hi = 0;
+    for (int i = tid; i < kBcSpread * kBcNibbleTable; i += nt) {
+        const int k = i / kBcNibbleTable, v = i % kBcNibbleTable;
+        const uint32_t weight = k < 4 ? 4u << k : 36u;
+        uint32_t e = 0;
 #pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            lo |= (uint32_t)((v >> m) & 1) << (8 * m + k + 2);
-            hi |= (uint32_t)((v >> (m + 4)) & 1) << (8 * m + k + 2);
-        }
-        s_spread[i] = make_uint2(lo, hi);
+        for (int m = 0; m < 4; ++m)
+            e += (uint32_t)((v >> m) & 1) * (weight << (8 * m));
+        s_nib[i] = e;
     }
 }
 
 // Blume-Capel: new (n, p) target words.  Neighbour planes nbn/nbp hold the
 // up, down, same and side words.  The field h + 4 = #(+1 neighbours) +
-// #(neighbours != -1) is summed bit-sliced into g0..g3; each site accepts iff
-// (u >> 1) < its table entry (2^31 = always).  Proposal: p' = b & ~(n & p),
-// n' = ~n | (p ^ b) with b = u & 1.
+// #(neighbours != -1) is summed bit-sliced into g0..g3.  kFull: a site
+// accepts iff u <= its entry; otherwise iff (u >> 1) < its entry (BcTable).
+// Proposal: p' = b & ~(n & p), n' = ~n | (p ^ b) with b = u & 1.
+template <bool kFull>
 __device__ __forceinline__ void bc_word_update(uint32_t &n, uint32_t &p, const uint32_t (&nbn)[4],
                                                const uint32_t (&nbp)[4], uint64_t q0,
                                                const PhiloxLaunch &pc, const uint32_t *s_thr,
-                                               const uint2 *s_spread)
+                                               const uint32_t *s_nib)
 {
     // eight indicators: s_i = +1 (n & p), s_i != -1 (~n | p)
     const uint32_t x0 = nbn[0] & nbp[0], x1 = ~nbn[0] | nbp[0];
@@ -147,45 +151,52 @@ __device__ __forceinline__ void bc_word_update(uint32_t &n, uint32_t &p, const u
     const uint32_t g2 = ce ^ cf;  // weight-4 column
     const uint32_t g3 = ce & cf;  // only when h + 4 = 8
     const uint32_t planes[kBcSpread] = {g0, g1, g2, g3, p, n};
+    // byte m of ev[k] (od[k]): nibble 2m (2m + 1) of plane k, times 4 -- the
+    // byte offset of its entry in table k
+    uint32_t ev[kBcSpread], od[kBcSpread];
+#pragma unroll
+    for (int k = 0; k < kBcSpread; ++k) {
+        ev[k] = (planes[k] << 2) & 0x3C3C3C3Cu;
+        od[k] = (planes[k] >> 2) & 0x3C3C3C3Cu;
+    }
 
     const char *thr_bytes = reinterpret_cast<const char *>(s_thr);
+    const char *nib_bytes = reinterpret_cast<const char *>(s_nib);
     const PhiloxWordPart wp = philox_word_part(pc, (uint32_t)(q0 >> 32));
-    uint32_t rej = 0, bits = 0;
+    // one chain over the 32 sites, site 31 first: acc ends with site b at
+    // bit b; bits (a right funnel shift) with site b at bit 31 - b
+    uint32_t acc = 0, bits = 0;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        // scaled table index of sites 8j .. 8j+7, one byte each
-        uint32_t lo = 0, hi = 0;
+    for (int i = 7; i >= 0; --i) {
+        // 4 (g + 9 (n + p)) of sites 4i .. 4i+3, one byte each
+        const uint32_t *src = (i & 1) ? od : ev;
+        uint32_t word = 0;
 #pragma unroll
         for (int k = 0; k < kBcSpread; ++k) {
-            const uint2 e = s_spread[k * 256 + ((planes[k] >> (8 * j)) & 0xFFu)];
-            lo |= e.x;
-            hi |= e.y;
+            const uint32_t off = __byte_perm(src[k], 0u, 0x4440u | (uint32_t)(i >> 1));
+            word += *reinterpret_cast<const uint32_t *>(nib_bytes + k * 4 * kBcNibbleTable + off);
         }
+        uint32_t r[4];
+        philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
 #pragma unroll
-        for (int i = 0; i < 2; ++i) {
-            uint32_t r[4];
-            philox_site4(pc, wp, (uint32_t)q0 + 2 * j + i, r[0], r[1], r[2], r[3]);
-            const uint32_t word = i ? hi : lo;
-            uint32_t nr = 0, nb = 0;
-#pragma unroll
-            for (int kk = 3; kk >= 0; --kk) {
-                // byte kk of word (the site's index) and bit 0 of u (b) at bit 8
-                const uint32_t off = __byte_perm(word, r[kk], 0x0040u | (uint32_t)kk) & 0x1FCu;
-                const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
-                nr = shift_in_not_below(nr, r[kk] >> 1, thr);
-                nb = (nb << 1) | (r[kk] & 1u);
-            }
-            const int sh = 8 * j + 4 * i;
-            rej = nr * (1u << sh) + rej;
-            bits = nb * (1u << sh) + bits;
+        for (int kk = 3; kk >= 0; --kk) {
+            // byte kk of word (the site's index) and bit 0 of u (b) at bit 8
+            const uint32_t off = __byte_perm(word, r[kk], 0x0040u | (uint32_t)kk) & 0x1FCu;
+            const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
+            if (kFull)
+                acc = shift_in_not_below(acc, thr, r[kk]);       // + (entry >= u): accept
+            else
+                acc = shift_in_not_below(acc, r[kk] >> 1, thr);  // + (v >= entry): reject
+            bits = __funnelshift_r(bits, r[kk], 1);
         }
     }
-    const uint32_t acc = ~rej;
+    const uint32_t accept = kFull ? acc : ~acc;
+    bits = __brev(bits);
     const uint32_t np2 = bits & ~(n & p);
     const uint32_t nn2 = ~n | (p ^ bits);
     const uint32_t n_old = n, p_old = p;
-    n = n_old ^ (acc & (n_old ^ nn2));
-    p = p_old ^ (acc & (p_old ^ np2));
+    n = n_old ^ (accept & (n_old ^ nn2));
+    p = p_old ^ (accept & (p_old ^ np2));
 }
 
 }  // namespace isg

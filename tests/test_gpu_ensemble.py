@@ -74,6 +74,25 @@ def test_mixed_ensemble_matches_lattices_alone(isg, orc):
         assert np.array_equal(ens.get(r), s)
 
 
+def test_blume_capel_never_accepted_moves_in_ensemble(isg):
+    """Per-sweep tables where some Blume-Capel moves can never be accepted
+    (beta = 10, inf) between ordinary ones: shared-memory replicas equal the
+    lattices swept alone."""
+    Ls, delta = [64, 256, 512], 1.9
+    seeds = [wl.BASE_SEED + 650 + r for r in range(len(Ls))]
+    betas = np.array([0.6, 10.0, 0.6, np.inf, 0.8, 3.0] * 4)
+    ens = isg.Ensemble(Ls, seeds, models=[1] * len(Ls), delta=delta, record_capacity=8)
+    ens.init_random()
+    ens.sweep(len(betas), betas=betas, record_every=6)
+    rows = ens.read_records()
+    for r, (L, sd) in enumerate(zip(Ls, seeds)):
+        recs, s = _alone(isg, L, 1, sd, betas, 6, delta)
+        for k, rec in enumerate(recs):
+            _same_obs(rows[k][r], rec)
+        assert np.array_equal(ens.get(r), s)
+    ens.close()
+
+
 def test_ensemble_workload_subset_and_xi2(isg, orc):
     """The replica-ensemble workload (uneven mix of L in {64..1024}, hot start
     quenched to beta_c), 64 replicas covering all sizes, 300 sweeps recorded

@@ -135,6 +135,20 @@ def test_blume_capel_crystal_field(isg, orc, delta, T):
     assert np.array_equal(lat.get(), s)
 
 
+def test_blume_capel_moves_never_accepted(isg, orc):
+    """Blume-Capel at beta so large that some thresholds round to 0 (the move
+    is never taken): the kernels switch to the (u >> 1) < thr31 compare for
+    those sweeps.  beta(t) alternates between such sweeps, beta = inf and
+    ordinary ones, so both compare forms follow each other on one lattice."""
+    L, seed, delta = 192, wl.BASE_SEED + 310, 1.9
+    lat, s = _pair(isg, orc, 1, L, seed, delta=delta)
+    betas = [0.6, 10.0, 0.6, math.inf, 0.8, 3.0] * 5
+    bmq, R, C = orc.run(s, 1, seed, 0, betas, delta=delta, record_every=1)
+    lat.sweep(len(betas), betas=betas, record_every=1)
+    _compare_records(lat.read_records(), bmq, R, C)
+    assert np.array_equal(lat.get(), s)
+
+
 @pytest.mark.parametrize("model", [0, 1])
 def test_schedule_and_per_sweep_betas(isg, orc, model):
     """Pre-cooling bath (Table II): T1 until t_switch, then T2; and beta(t) arrays."""
