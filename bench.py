@@ -39,11 +39,16 @@ from paper_2503_14688_b300 import workloads as wl  # noqa: E402
 METRIC = "spin flips/ns per B300 (Ising, BC) & % roofline; batched/served vs single lattice"
 UNIT = "flips/ns"
 
-# Algorithmic integer operations per site update:
-# Philox4x32-10 per 4 sites = 20 wide multiplies + 20 three-input XORs;
-# the acceptance compares: Ising 2 per site, Blume-Capel 1 per site plus the
-# proposal bit.  Units: one 32-lane-issue integer operation.
-ALG_OPS_PER_SITE = {wl.ISING: 10.0 + 2.0, wl.BLUME_CAPEL: 10.0 + 2.0}
+# Algorithmic integer operations per site update (one 32-lane-issue integer
+# operation each; a wide multiply counts once):
+#   Philox4x32-10 per 4 sites: 20 wide (32x32->64) multiplies + 20
+#   three-input XORs, i.e. 5 + 5 per site;
+#   Ising acceptance: 2 threshold compares + 2 bit inserts; the bit-sliced
+#   neighbour count and flip logic: about 1 per site (30-40 per 32 sites);
+#   total 15;
+#   Blume-Capel: the same Philox plus the spin-1 acceptance (about six
+#   compares over the candidate energies) and the two-plane update: about 25.
+ALG_OPS_PER_SITE = {wl.ISING: 15.0, wl.BLUME_CAPEL: 25.0}
 SMS = 148
 INT_LANES_PER_SM = 128     # 4 SMSPs x 32 lanes, one warp-instruction per SMSP per clock
 # The pipe that binds the half-sweep: the 32x32->64 multiplies of Philox run
@@ -53,11 +58,11 @@ WIDE_MUL_PER_SM_CLK = 32
 WIDE_MUL_PER_SITE = 18 / 4
 # DRAM bytes (read + write) per site of one half-sweep launch, from one ncu
 # capture of the current kernels on a smaller lattice (Ising L = 2^16:
-# 536.9 + 229.4 MB per 2^31 sites; Blume-Capel L = 2^15: 274.1 + 93.6 MB per
+# 536.9 + 229.4 MB per 2^31 sites; Blume-Capel L = 2^15: 274.5 + 93.2 MB per
 # 2^29 sites), scaled to a full launch by the sites it updates.  Against the
 # algorithmic 0.375 (Ising) and 0.75 (Blume-Capel) B per site.
 DRAM_BYTES_PER_SITE = {wl.ISING: (536.9e6 + 229.4e6) / 2**31,
-                       wl.BLUME_CAPEL: (274.1e6 + 93.6e6) / 2**29}
+                       wl.BLUME_CAPEL: (274.5e6 + 93.2e6) / 2**29}
 
 
 def _l2_note(lattice_bytes):
