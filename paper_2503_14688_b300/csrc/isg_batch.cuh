@@ -4,9 +4,14 @@
 //
 // Each CTA takes whole lattices from a global work counter (in the order the
 // host gives, largest first), copies the lattice's spin planes into shared
-// memory, runs its sweeps there with a __syncthreads between half-sweeps --
-// no wait on any other CTA -- records observables, and writes the planes
-// back.  Included by one translation unit each (anonymous namespace).
+// memory, runs its sweeps there with a barrier between half-sweeps -- no
+// wait on any other CTA -- records observables, and writes the planes back.
+// Once the counter reaches the lattices that fit half the CTA's shared
+// memory, the CTA splits into two teams of half its threads, each with its
+// own half of the shared memory and its own named barrier, which take
+// lattices independently: while one team runs the last, partly idle round of
+// a half-sweep, the other keeps the SM's pipes busy.  Included by one
+// translation unit each (anonymous namespace).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -61,6 +66,29 @@ struct EnsArgs {
     uint32_t t0;
     int32_t nsweeps;
     int32_t record_every;
+    // half_words > 0: order entries from split_from on need at most
+    // half_words 32-bit words of shared memory and run on half-CTA teams
+    uint32_t half_words;
+    int32_t split_from;
+};
+
+// The threads that work on one lattice.  kHalf = false: the whole CTA,
+// synchronised by __syncthreads.  kHalf = true: one of two teams of half the
+// CTA (team 0 = the lower threads), synchronised by named barrier 1 + team.
+// Every field derives from threadIdx.x and blockDim.x, so the compiler can
+// recompute it instead of keeping it in a register.
+template <bool kHalf>
+struct Team {
+    __device__ __forceinline__ int nt() const { return kHalf ? (int)(blockDim.x >> 1) : (int)blockDim.x; }
+    __device__ __forceinline__ int team() const { return kHalf ? (int)(threadIdx.x >= (blockDim.x >> 1)) : 0; }
+    __device__ __forceinline__ int tid() const { return (int)threadIdx.x - team() * nt(); }
+    __device__ __forceinline__ void sync() const
+    {
+        if (kHalf)
+            asm volatile("bar.sync %0, %1;" ::"r"(1 + team()), "r"(nt()) : "memory");
+        else
+            __syncthreads();
+    }
 };
 
 size_t smem_bytes_for(int32_t model, int64_t L)
@@ -73,11 +101,11 @@ size_t smem_bytes_for(int32_t model, int64_t L)
 // ---------------------------------------------------------------------------
 // Observables of the replica held in shared memory (after a full sweep).
 // ---------------------------------------------------------------------------
-template <int MODEL>
-__device__ void smem_measure(const uint32_t *P, int L, int W, int32_t *R_s, int32_t *C_s,
-                             unsigned long long *acc, uint8_t *rec, int64_t sweep)
+template <int MODEL, bool kHalf>
+__device__ void smem_measure(const Team<kHalf> &team, const uint32_t *P, int L, int W, int32_t *R_s,
+                             int32_t *C_s, unsigned long long *acc, uint8_t *rec, int64_t sweep)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = team.tid(), nt = team.nt();
     const int LW = L * W;
     for (int i = tid; i < L; i += nt) {
         R_s[i] = 0;
@@ -85,7 +113,7 @@ __device__ void smem_measure(const uint32_t *P, int L, int W, int32_t *R_s, int3
     }
     if (tid < 3)
         acc[tid] = 0;
-    __syncthreads();
+    team.sync();
     const uint32_t *p0 = MODEL == 0 ? P : P + LW;
     const uint32_t *p1 = MODEL == 0 ? P + LW : P + 3 * LW;
     const uint32_t *n0 = P, *n1 = P + 2 * LW;
@@ -187,7 +215,7 @@ __device__ void smem_measure(const uint32_t *P, int L, int W, int32_t *R_s, int3
                 atomicAdd(&C_s[x + 1], vo);
         }
     }
-    __syncthreads();
+    team.sync();
     int64_t *hdr = reinterpret_cast<int64_t *>(rec);
     int32_t *R = reinterpret_cast<int32_t *>(rec + 32);
     int32_t *C = R + L;
@@ -201,7 +229,7 @@ __device__ void smem_measure(const uint32_t *P, int L, int W, int32_t *R_s, int3
         R[i] = R_s[i];
         C[i] = C_s[i];
     }
-    __syncthreads();
+    team.sync();
 }
 
 // One Blume-Capel colour of a replica held in shared memory; the threads
@@ -238,10 +266,10 @@ __device__ __forceinline__ void bc_smem_colour(uint32_t *P, int L, int W, int c,
     }
 }
 
-template <int MODEL>
-__device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
+template <int MODEL, bool kHalf>
+__device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem, const Team<kHalf> &team)
 {
-    const int tid = threadIdx.x, nt = blockDim.x;
+    const int tid = team.tid(), nt = team.nt();
     const int L = it.L, W = L / 64, LW = L * W;
     const int nplanes = MODEL == 0 ? 2 : 4;
     uint32_t *P = smem;
@@ -257,7 +285,7 @@ __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
         s4[i] = g4[i];
     if (MODEL == 1)
         bc_spread_fill(s_nib, tid, nt);
-    __syncthreads();
+    team.sync();
 
     const int dy = nt / W, dw = nt - (nt / W) * W;
     const uint64_t qrow = (uint64_t)(L / 8);
@@ -277,7 +305,7 @@ __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
             for (int i = tid; i < kBcTableSize; i += nt)
                 s_thr[i] = btab[s].thr[i];
             bc_full = btab[s].full != 0;
-            __syncthreads();
+            team.sync();
         }
         for (int c = 0; c < 2; ++c) {
             const PhiloxLaunch pc = philox_consts_device(it.seed, t, (uint32_t)c);
@@ -307,39 +335,71 @@ __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem)
             } else {
                 bc_smem_colour<false>(P, L, W, c, y, w, dy, dw, qrow, pc, s_thr, s_nib);
             }
-            __syncthreads();
+            team.sync();
         }
         if (record_every > 0 && (s + 1) % record_every == 0) {
             const int k = (s + 1) / record_every - 1;
             const int row = (rec_row0 + k) % rec_cap;
             uint8_t *rec = rec_base + (uint64_t)row * rec_pitch;
-            smem_measure<MODEL>(P, L, W, R_s, C_s, acc, rec, (int64_t)t + 1);
+            smem_measure<MODEL, kHalf>(team, P, L, W, R_s, C_s, acc, rec, (int64_t)t + 1);
         }
     }
     uint4 *o4 = reinterpret_cast<uint4 *>(it.planes);
     for (int i = tid; i < nplanes * LW / 4; i += nt)
         o4[i] = s4[i];
-    __syncthreads();
+    team.sync();
+}
+
+template <bool kHalf>
+__device__ __forceinline__ void run_item(const EnsArgs &a, int item, uint32_t *smem)
+{
+    const EnsItem it = a.items[a.order[item]];
+    const Team<kHalf> team;
+    if (it.model == 0)
+        run_replica<0, kHalf>(it, a, smem, team);
+    else
+        run_replica<1, kHalf>(it, a, smem, team);
 }
 
 __global__ void __launch_bounds__(1024, 1) k_ensemble(const EnsArgs *__restrict__ args)
 {
     extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ int s_item;
+    __shared__ int s_item[3];
     const EnsArgs a = *args;
+    const bool split = a.half_words > 0 && blockDim.x % 64 == 0;
+    int item;
+    // whole-CTA lattices (all of them without a split)
     for (;;) {
         if (threadIdx.x == 0)
-            s_item = atomicAdd(a.counter, 1);
+            s_item[0] = atomicAdd(a.counter, 1);
         __syncthreads();
-        const int item = s_item;
+        item = s_item[0];
         __syncthreads();
         if (item >= a.n_order)
+            return;
+        if (split && item >= a.split_from)
             break;
-        const EnsItem it = a.items[a.order[item]];
-        if (it.model == 0)
-            run_replica<0>(it, a, smem);
-        else
-            run_replica<1>(it, a, smem);
+        run_item<false>(a, item, smem);
+    }
+    // two teams from here on; team 0 starts with the lattice just taken.
+    // Control flow below is uniform within a team (the item comes from the
+    // team's shared slot), so each named barrier sees all of its warps.
+    const Team<true> team;
+    const int g = team.team();
+    uint32_t *tsm = smem + (size_t)g * a.half_words;
+    int mine = g == 0 ? item : -1;
+    for (;;) {
+        if (mine < 0) {
+            if (team.tid() == 0)
+                s_item[1 + g] = atomicAdd(a.counter, 1);
+            team.sync();
+            mine = s_item[1 + g];
+            team.sync();
+        }
+        if (mine >= a.n_order)
+            return;
+        run_item<true>(a, mine, tsm);
+        mine = -1;
     }
 }
 

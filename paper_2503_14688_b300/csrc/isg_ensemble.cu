@@ -77,6 +77,8 @@ struct isg_ensemble {
     EnsItem *d_items = nullptr;
     int32_t *d_order = nullptr;
     int32_t n_smem = 0;
+    int32_t split_from = 0;   // order index of the first lattice run by half-CTA teams
+    uint32_t half_words = 0;  // shared memory of one team (32-bit words); 0: no teams
     std::vector<int64_t> global_list;
     int32_t *d_counter = nullptr;
     EnsArgs *d_args = nullptr;
@@ -167,6 +169,8 @@ isg_status queue_sweeps(isg_ensemble *e, int64_t n, int64_t record_every, int64_
         a.t0 = (uint32_t)e->t;
         a.nsweeps = (int32_t)n;
         a.record_every = (int32_t)record_every;
+        a.half_words = e->half_words;
+        a.split_from = e->split_from;
         ECUDA(cudaMemcpyAsync(e->d_args, e->h_args, sizeof(EnsArgs), cudaMemcpyHostToDevice, st),
               "ensemble args");
         ECUDA(cudaMemsetAsync(e->d_counter, 0, sizeof(int32_t), st), "work counter");
@@ -275,10 +279,27 @@ isg_status isg_ensemble_create(const isg_ensemble_desc *d, isg_ensemble **out)
             e->global_list.push_back(r);
         }
     }
+    // largest shared-memory need first (longest-processing-time order; the
+    // need grows with the work, L^2 sites at 1 or 2 bits)
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        return e->L[a] * e->L[a] * (e->model[a] + 1) > e->L[b] * e->L[b] * (e->model[b] + 1);
+        return smem_bytes_for(e->model[a], e->L[a]) > smem_bytes_for(e->model[b], e->L[b]);
     });
     e->n_smem = (int32_t)order.size();
+    // lattices that fit half the largest shared-memory request run on
+    // half-CTA teams (isg_batch.cuh); the request covers two of them
+    const size_t half_cap = ((size_t)kBatchSmemMax / 2) & ~(size_t)15;
+    e->split_from = e->n_smem;
+    for (int32_t i = 0; i < e->n_smem; ++i)
+        if (smem_bytes_for(e->model[order[i]], e->L[order[i]]) <= half_cap) {
+            e->split_from = i;
+            break;
+        }
+    if (e->split_from < e->n_smem) {
+        const size_t half_bytes =
+            (smem_bytes_for(e->model[order[e->split_from]], e->L[order[e->split_from]]) + 15) & ~(size_t)15;
+        e->half_words = (uint32_t)(half_bytes / 4);
+        smem = std::max(smem, 2 * half_bytes);
+    }
     std::vector<EnsItem> items(d->n);
     for (int64_t r = 0; r < d->n; ++r) {
         items[r].seed = e->seed[r];
@@ -553,6 +574,8 @@ isg_status isg_ensemble_autotune(isg_ensemble *e, int64_t sweeps, int32_t *threa
         args.t0 = 0;
         args.nsweeps = (int32_t)sweeps;
         args.record_every = 0;
+        args.half_words = e->half_words;
+        args.split_from = e->split_from;
         *e->h_args = args;
         err = cudaMemcpy(e->d_args, e->h_args, sizeof(EnsArgs), cudaMemcpyHostToDevice);
         const int blocks = occupancy_blocks(nt, e->smem);
