@@ -188,22 +188,27 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) k_sw_local_w(Planes pl, u
     bool ok = true;
     int s_prev = 0;
     uint32_t uy_prev = 0, hm_prev = 0;
-    const PhiloxLaunch &pc = (tx & 1) ? py : px;
     // all spins of the tile first: independent loads, issued together
 #pragma unroll 8
     for (int r = 0; r < kTileH; ++r)
         s_sp[wid][r][tx] = (int8_t)spin_at(pl, x, by * kTileH + r);
     __syncwarp();
+    // The bond words of two rows come from one Philox call per lane: lane
+    // 16 h + 2 m + d draws for sites 4m .. 4m+3 of row r2 + h, the +x bonds
+    // (stream px) for d = 0 and the +y bonds (py) for d = 1.
+    const int hsel = tx >> 4, jsel = tx & 15;
+    const PhiloxLaunch &pc = (jsel & 1) ? py : px;
+    uint32_t w[4];
 #pragma unroll 1
     for (int r = 0; r < kTileH; ++r) {
         const int64_t y = by * kTileH + r;
         const int sv = s_sp[wid][r][tx];
-        const int64_t g = (y * L + bx * kTile + (tx & ~3)) >> 2;
-        uint32_t w[4] = {0u, 0u, 0u, 0u};
-        if ((tx & 3) < 2)
+        if ((r & 1) == 0) {
+            const int64_t g = ((y + hsel) * L + bx * kTile + 4 * (jsel >> 1)) >> 2;
             philox_site4(pc, philox_word_part(pc, (uint32_t)((uint64_t)g >> 32)), (uint32_t)g, w[0],
                          w[1], w[2], w[3]);
-        const int src = tx & ~3;
+        }
+        const int src = 16 * (r & 1) + 2 * (tx >> 2);
         uint32_t ux = 0, uy = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
