@@ -100,6 +100,9 @@ struct isg_ensemble {
 
 namespace {
 
+// Largest number of single-lattice launches one sweep call puts in a graph.
+constexpr int64_t kMaxGraphLaunches = (int64_t)1 << 16;
+
 void free_tables(isg_ensemble *e)
 {
     if (e->d_ithr) cudaFree(e->d_ithr);
@@ -398,9 +401,27 @@ isg_status isg_ensemble_sweep(isg_ensemble *e, int64_t n, const double *betas, d
             bc_table(b, e->delta, &e->h_btab[i]);
     }
     const int64_t row0 = (e->rec_head + e->rec_count) % e->rec_cap;
+    cudaStream_t st = e->stream;
+    // replicas too large for shared memory cost one launch per half-sweep
+    // (and record); beyond kMaxGraphLaunches the graph's host memory would
+    // grow without bound, so such a call is queued on the stream directly
+    const int64_t global_launches =
+        (int64_t)e->global_list.size() * (2 * n + (record_every > 0 ? n / record_every : 0));
+    if (global_launches > kMaxGraphLaunches) {
+        ECUDA(cudaMemcpyAsync(e->d_ithr, e->h_ithr, sizeof(IsingThr) * n, cudaMemcpyHostToDevice, st),
+              "threshold upload");
+        if (e->h_btab)
+            ECUDA(cudaMemcpyAsync(e->d_btab, e->h_btab, sizeof(BcTable) * n, cudaMemcpyHostToDevice, st),
+                  "threshold upload");
+        isg_status qs = queue_sweeps(e, n, record_every, row0);
+        if (qs != ISG_OK)
+            return qs;
+        e->t += n;
+        e->rec_count += nrec;
+        return ISG_OK;
+    }
     // capture this call's device work in a graph and replay it; a later call
     // with the same shape updates the instantiated graph in place
-    cudaStream_t st = e->stream;
     ECUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t ce = cudaMemcpyAsync(e->d_ithr, e->h_ithr, sizeof(IsingThr) * n,
                                      cudaMemcpyHostToDevice, st);

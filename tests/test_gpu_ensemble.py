@@ -93,6 +93,27 @@ def test_blume_capel_never_accepted_moves_in_ensemble(isg):
     ens.close()
 
 
+def test_many_global_path_launches_run_without_a_graph(isg):
+    """Replicas too large for shared memory (Blume-Capel L = 1024) cost one
+    launch per half-sweep; a call with more than 2^16 of them is queued on
+    the stream instead of captured.  Its replicas equal lattices alone."""
+    n_rep, n = 36, 1000  # 36 x (2 x 1000 + 100 records) launches
+    Ls = [1024] * n_rep
+    seeds = [wl.BASE_SEED + 700 + r for r in range(n_rep)]
+    betas = np.full(n, 1 / wl.T_C_BLUME_CAPEL)
+    ens = isg.Ensemble(Ls, seeds, models=[1] * n_rep, delta=0.0, record_capacity=101)
+    ens.init_random()
+    ens.sweep(n, betas=betas, record_every=10)
+    rows = ens.read_records()
+    assert len(rows) == 100
+    for r in (0, 17, 35):
+        recs, s = _alone(isg, 1024, 1, seeds[r], betas, 10)
+        for k in (0, 49, 99):
+            _same_obs(rows[k][r], recs[k])
+        assert np.array_equal(ens.get(r), s)
+    ens.close()
+
+
 def test_ensemble_workload_subset_and_xi2(isg, orc):
     """The replica-ensemble workload (uneven mix of L in {64..1024}, hot start
     quenched to beta_c), 64 replicas covering all sizes, 300 sweeps recorded
