@@ -80,6 +80,15 @@ struct isg_ensemble {
     int32_t split_from = 0;   // order index of the first lattice run by half-CTA teams
     uint32_t half_words = 0;  // shared memory of one team (32-bit words); 0: no teams
     std::vector<int64_t> global_list;
+    // the global-path replicas grouped by (model, L), swept by one multi-
+    // lattice launch per group and half-sweep
+    struct GlobalGroup {
+        int32_t model;
+        int64_t L;
+        std::vector<uint32_t *> planes;
+        std::vector<uint64_t> seeds;
+    };
+    std::vector<GlobalGroup> groups;
     int32_t *d_counter = nullptr;
     EnsArgs *d_args = nullptr;
     EnsArgs *h_args = nullptr;  // pinned
@@ -100,8 +109,10 @@ struct isg_ensemble {
 
 namespace {
 
-// Largest number of single-lattice launches one sweep call puts in a graph.
+// Largest number of launches one sweep call puts in a graph; multi-lattice
+// launches carry 24 KB of parameters each, so fewer of them.
 constexpr int64_t kMaxGraphLaunches = (int64_t)1 << 16;
+constexpr int64_t kMaxGraphMultiLaunches = 2048;
 
 void free_tables(isg_ensemble *e)
 {
@@ -180,21 +191,20 @@ isg_status queue_sweeps(isg_ensemble *e, int64_t n, int64_t record_every, int64_
         k_ensemble<<<e->blocks, e->threads, e->smem, st>>>(e->d_args);
         ECUDA(cudaGetLastError(), "ensemble launch");
     }
-    for (int64_t r : e->global_list) {
-        const Planes pl = replica_planes(e, r);
-        for (int64_t i = 0; i < n; ++i) {
-            const uint32_t t = (uint32_t)(e->t + i);
-            for (int c = 0; c < 2; ++c) {
-                PhiloxLaunch ph;
-                philox_launch_consts(e->seed[r], t, (uint32_t)c, &ph);
-                ECUDA(launch_half_sweep(pl, c, ph, e->h_ithr[i], e->h_btab ? &e->h_btab[i] : nullptr, st),
+    for (int64_t i = 0; i < n && !e->groups.empty(); ++i) {
+        const uint32_t t = (uint32_t)(e->t + i);
+        for (int c = 0; c < 2; ++c)
+            for (const auto &gr : e->groups)
+                ECUDA(launch_half_sweep_multi(gr.model, gr.L, gr.planes.data(), gr.seeds.data(),
+                                              (int)gr.planes.size(), t, c, e->h_ithr[i],
+                                              e->h_btab ? &e->h_btab[i] : nullptr, st),
                       "half-sweep launch");
-            }
-            if (record_every > 0 && (i + 1) % record_every == 0) {
-                const int64_t row = (rec_row0 + (i + 1) / record_every - 1) % e->rec_cap;
+        if (record_every > 0 && (i + 1) % record_every == 0) {
+            const int64_t row = (rec_row0 + (i + 1) / record_every - 1) % e->rec_cap;
+            for (int64_t r : e->global_list) {
                 uint8_t *rec = e->rec_ring + (uint64_t)row * e->row_bytes + e->rec_off[r];
                 ECUDA(cudaMemsetAsync(rec, 0, record_stride(e->L[r]), st), "record clear");
-                ECUDA(launch_measure(pl, rec, (int64_t)t + 1, st), "measure launch");
+                ECUDA(launch_measure(replica_planes(e, r), rec, (int64_t)t + 1, st), "measure launch");
             }
         }
     }
@@ -288,6 +298,17 @@ isg_status isg_ensemble_create(const isg_ensemble_desc *d, isg_ensemble **out)
         return smem_bytes_for(e->model[a], e->L[a]) > smem_bytes_for(e->model[b], e->L[b]);
     });
     e->n_smem = (int32_t)order.size();
+    for (int64_t r : e->global_list) {
+        auto it = std::find_if(e->groups.begin(), e->groups.end(), [&](const isg_ensemble::GlobalGroup &gr) {
+            return gr.model == e->model[r] && gr.L == e->L[r];
+        });
+        if (it == e->groups.end()) {
+            e->groups.push_back({e->model[r], e->L[r], {}, {}});
+            it = e->groups.end() - 1;
+        }
+        it->planes.push_back(reinterpret_cast<uint32_t *>(e->planes + e->plane_off[r]));
+        it->seeds.push_back(e->seed[r]);
+    }
     // lattices that fit half the largest shared-memory request run on
     // half-CTA teams (isg_batch.cuh); the request covers two of them
     const size_t half_cap = ((size_t)kBatchSmemMax / 2) & ~(size_t)15;
@@ -405,9 +426,13 @@ isg_status isg_ensemble_sweep(isg_ensemble *e, int64_t n, const double *betas, d
     // replicas too large for shared memory cost one launch per half-sweep
     // (and record); beyond kMaxGraphLaunches the graph's host memory would
     // grow without bound, so such a call is queued on the stream directly
+    int64_t multi_per_sweep = 0;
+    for (const auto &gr : e->groups)
+        multi_per_sweep += 2 * (((int64_t)gr.planes.size() + kMultiMax - 1) / kMultiMax);
+    const int64_t multi_launches = multi_per_sweep * n;
     const int64_t global_launches =
-        (int64_t)e->global_list.size() * (2 * n + (record_every > 0 ? n / record_every : 0));
-    if (global_launches > kMaxGraphLaunches) {
+        multi_launches + (int64_t)e->global_list.size() * (record_every > 0 ? n / record_every : 0);
+    if (global_launches > kMaxGraphLaunches || multi_launches > kMaxGraphMultiLaunches) {
         ECUDA(cudaMemcpyAsync(e->d_ithr, e->h_ithr, sizeof(IsingThr) * n, cudaMemcpyHostToDevice, st),
               "threshold upload");
         if (e->h_btab)

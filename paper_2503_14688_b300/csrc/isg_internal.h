@@ -95,6 +95,14 @@ cudaError_t launch_init_uniform(const Planes &pl, int value, cudaStream_t st);
 cudaError_t launch_half_sweep(const Planes &pl, int colour, const PhiloxLaunch &ph,
                               const IsingThr &ithr, const BcTable *btab, cudaStream_t st);
 cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaStream_t st);
+// One half-sweep of colour `colour` at sweep t of n lattices of one model
+// and side L (planes[i], seeds[i]) in as few launches as the kernel
+// parameters allow (kMultiMax lattices each); same results as n single
+// launches.
+constexpr int kMultiMax = 240;  // lattices per launch: 240 x 100 B of parameters
+cudaError_t launch_half_sweep_multi(int model, int64_t L, uint32_t *const *planes, const uint64_t *seeds,
+                                    int n, uint32_t t, int colour, const IsingThr &ithr,
+                                    const BcTable *btab, cudaStream_t st);
 cudaError_t launch_correlation(const Planes &pl, int nr, const int64_t *d_r, unsigned long long *d_out,
                                cudaStream_t st);
 cudaError_t launch_pack(const Planes &pl, const int8_t *d_spins, int32_t *d_bad, cudaStream_t st);

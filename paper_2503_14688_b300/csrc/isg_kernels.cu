@@ -187,17 +187,16 @@ __global__ void k_init_uniform(Planes pl, int value)
 // once per band plus two halo rows).
 // ---------------------------------------------------------------------------
 template <int V>
-__global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
-    k_ising_half(uint32_t *__restrict__ tgt, const uint32_t *__restrict__ nbr, int64_t L,
-                 int64_t W, int colour, int H, PhiloxLaunch pc, IsingThr thr)
+__device__ __forceinline__ void ising_half_band(uint32_t g, uint32_t *__restrict__ tgt,
+                                                const uint32_t *__restrict__ nbr, uint32_t Li,
+                                                uint32_t Wi, int colour, int H, const PhiloxLaunch &pc,
+                                                const IsingThr &thr)
 {
     // threads enumerate (row band, V-word group) pairs, groups fastest, so
     // every block is full whatever the row width; rows and words fit 32 bits
-    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
-    const uint32_t tpr = (uint32_t)W / V;
+    const uint32_t tpr = Wi / V;
     const uint32_t band = g / tpr;
     const uint32_t w0 = (g - band * tpr) * V;
-    const uint32_t Li = (uint32_t)L, Wi = (uint32_t)W;
     const uint32_t y0 = band * (uint32_t)H;
     if (y0 >= Li)
         return;
@@ -230,6 +229,34 @@ __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
     }
 }
 
+template <int V>
+__global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
+    k_ising_half(uint32_t *__restrict__ tgt, const uint32_t *__restrict__ nbr, int64_t L,
+                 int64_t W, int colour, int H, PhiloxLaunch pc, IsingThr thr)
+{
+    ising_half_band<V>(blockIdx.x * blockDim.x + threadIdx.x, tgt, nbr, (uint32_t)L, (uint32_t)W,
+                       colour, H, pc, thr);
+}
+
+// Many lattices of one side L in one launch (the ensemble's replicas too
+// large for shared memory): lattice blockIdx.y of the launch, its planes and
+// Philox constants in the kernel parameters, so both stay uniform per block.
+struct MultiArgs {
+    PhiloxLaunch pc[kMultiMax];
+    uint32_t *planes[kMultiMax];
+};
+
+template <int V>
+__global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
+    k_ising_half_multi(int64_t L, int colour, int H, IsingThr thr, const __grid_constant__ MultiArgs a)
+{
+    const int r = blockIdx.y;
+    const uint32_t Li = (uint32_t)L, Wi = (uint32_t)(L / 64);
+    const uint64_t LW = (uint64_t)Li * Wi;
+    ising_half_band<V>(blockIdx.x * blockDim.x + threadIdx.x, a.planes[r] + colour * LW,
+                       a.planes[r] + (1 - colour) * LW, Li, Wi, colour, H, a.pc[r], thr);
+}
+
 // ---------------------------------------------------------------------------
 // Blume-Capel half-sweep.  Two bit-planes per colour: n (s != 0) and p (s > 0).
 // The neighbour field h + 4 = #(+1 neighbours) + #(neighbours != -1) is a
@@ -238,19 +265,13 @@ __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
 // (proposal bit, n + p, h + 4) and held in shared memory.
 // ---------------------------------------------------------------------------
 template <int V, bool kFull>
-__global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
-    k_bc_half(uint32_t *__restrict__ tn_plane, uint32_t *__restrict__ tp_plane,
-              const uint32_t *__restrict__ nn_plane, const uint32_t *__restrict__ np_plane,
-              int64_t L, int64_t W, int colour, int H, PhiloxLaunch pc, BcTable tab)
+__device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ tn_plane,
+                                             uint32_t *__restrict__ tp_plane,
+                                             const uint32_t *__restrict__ nn_plane,
+                                             const uint32_t *__restrict__ np_plane, int64_t L,
+                                             int64_t W, int colour, int H, const PhiloxLaunch &pc,
+                                             const uint32_t *s_thr, const uint32_t *s_nib)
 {
-    __shared__ uint32_t s_thr[kBcTableSize];
-    __shared__ uint32_t s_nib[kBcSpread * kBcNibbleTable];
-    for (int i = threadIdx.x; i < kBcTableSize; i += blockDim.x)
-        s_thr[i] = tab.thr[i];
-    bc_spread_fill(s_nib, threadIdx.x, blockDim.x);
-    __syncthreads();
-
-    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tpr = W / V;
     const int64_t band = g / tpr;
     const int64_t w0 = (g - band * tpr) * V;
@@ -289,6 +310,41 @@ __global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
         Sn = Dn;
         Sp = Dp;
     }
+}
+
+template <int V, bool kFull>
+__global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
+    k_bc_half(uint32_t *__restrict__ tn_plane, uint32_t *__restrict__ tp_plane,
+              const uint32_t *__restrict__ nn_plane, const uint32_t *__restrict__ np_plane,
+              int64_t L, int64_t W, int colour, int H, PhiloxLaunch pc, BcTable tab)
+{
+    __shared__ uint32_t s_thr[kBcTableSize];
+    __shared__ uint32_t s_nib[kBcSpread * kBcNibbleTable];
+    for (int i = threadIdx.x; i < kBcTableSize; i += blockDim.x)
+        s_thr[i] = tab.thr[i];
+    bc_spread_fill(s_nib, threadIdx.x, blockDim.x);
+    __syncthreads();
+    bc_half_band<V, kFull>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, tn_plane, tp_plane,
+                           nn_plane, np_plane, L, W, colour, H, pc, s_thr, s_nib);
+}
+
+// Blume-Capel lattices of one side L in one launch (see k_ising_half_multi).
+template <int V, bool kFull>
+__global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
+    k_bc_half_multi(int64_t L, int colour, int H, BcTable tab, const __grid_constant__ MultiArgs a)
+{
+    __shared__ uint32_t s_thr[kBcTableSize];
+    __shared__ uint32_t s_nib[kBcSpread * kBcNibbleTable];
+    for (int i = threadIdx.x; i < kBcTableSize; i += blockDim.x)
+        s_thr[i] = tab.thr[i];
+    bc_spread_fill(s_nib, threadIdx.x, blockDim.x);
+    __syncthreads();
+    const int r = blockIdx.y;
+    const int64_t W = L / 64, LW = L * W;
+    uint32_t *tn = a.planes[r] + (int64_t)(2 * colour) * LW;
+    const uint32_t *nn = a.planes[r] + (int64_t)(2 * (1 - colour)) * LW;
+    bc_half_band<V, kFull>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, tn, tn + LW, nn, nn + LW,
+                           L, W, colour, H, a.pc[r], s_thr, s_nib);
 }
 
 // ---------------------------------------------------------------------------
@@ -771,6 +827,60 @@ cudaError_t launch_half_sweep(const Planes &pl, int colour, const PhiloxLaunch &
     if (V >= 2)
         return launch_bc<2>(pl, colour, ph, *btab, st);
     return launch_bc<1>(pl, colour, ph, *btab, st);
+}
+
+cudaError_t launch_half_sweep_multi(int model, int64_t L, uint32_t *const *planes, const uint64_t *seeds,
+                                    int n, uint32_t t, int colour, const IsingThr &ithr,
+                                    const BcTable *btab, cudaStream_t st)
+{
+    const int64_t W = L / 64;
+    for (int i0 = 0; i0 < n; i0 += kMultiMax) {
+        const int m = n - i0 < kMultiMax ? n - i0 : kMultiMax;
+        MultiArgs a;
+        for (int i = 0; i < m; ++i) {
+            philox_launch_consts(seeds[i0 + i], t, (uint32_t)colour, &a.pc[i]);
+            a.planes[i] = planes[i0 + i];
+        }
+        if (model == 0) {
+            const int V = W % 4 == 0 ? 4 : (W % 2 == 0 ? 2 : 1);
+            const int64_t tpr = W / V;
+            // the band height that fills the GPU for one lattice, shortened
+            // by the m lattices of the launch sharing the waves
+            int H = sweep_band(L, tpr);
+            while (H < 64 && tpr * ((L + 2 * H - 1) / (2 * H)) * m >= 148LL * kSweepMinBlocks * kSweepThreads * 8)
+                H *= 2;
+            const dim3 grid(sweep_blocks(L, tpr, H), (unsigned)m);
+            if (V == 4)
+                k_ising_half_multi<4><<<grid, kSweepThreads, 0, st>>>(L, colour, H, ithr, a);
+            else if (V == 2)
+                k_ising_half_multi<2><<<grid, kSweepThreads, 0, st>>>(L, colour, H, ithr, a);
+            else
+                k_ising_half_multi<1><<<grid, kSweepThreads, 0, st>>>(L, colour, H, ithr, a);
+        } else {
+            const int V = W % 2 == 0 ? 2 : 1;
+            const int64_t tpr = W / V;
+            int H = sweep_band(L, tpr, kBcMinBlocks, kBcThreads, 2);
+            while (H < 64 && tpr * ((L + 2 * H - 1) / (2 * H)) * m >= 148LL * kBcMinBlocks * kBcThreads * 2)
+                H *= 2;
+            const int64_t threads = tpr * ((L + H - 1) / H);
+            const dim3 grid((unsigned)((threads + kBcThreads - 1) / kBcThreads), (unsigned)m);
+            if (V == 2) {
+                if (btab->full)
+                    k_bc_half_multi<2, true><<<grid, kBcThreads, 0, st>>>(L, colour, H, *btab, a);
+                else
+                    k_bc_half_multi<2, false><<<grid, kBcThreads, 0, st>>>(L, colour, H, *btab, a);
+            } else {
+                if (btab->full)
+                    k_bc_half_multi<1, true><<<grid, kBcThreads, 0, st>>>(L, colour, H, *btab, a);
+                else
+                    k_bc_half_multi<1, false><<<grid, kBcThreads, 0, st>>>(L, colour, H, *btab, a);
+            }
+        }
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaStream_t st)
