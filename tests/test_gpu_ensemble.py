@@ -93,6 +93,27 @@ def test_blume_capel_never_accepted_moves_in_ensemble(isg):
     ens.close()
 
 
+def test_multi_lattice_launches_with_odd_word_counts(isg):
+    """Global-path groups whose rows hold an odd number of words (Ising
+    L = 1344, Blume-Capel L = 960: one word per thread) and a Blume-Capel
+    group with a never-accepted move (beta = 10 at Delta = 1.9) equal the
+    lattices alone."""
+    Ls = [1344, 1344, 1344, 960, 960, 960]
+    models = [0, 0, 0, 1, 1, 1]
+    seeds = [wl.BASE_SEED + 760 + r for r in range(len(Ls))]
+    betas = np.array([0.4, 0.45, 10.0, 0.6, 0.5, 0.7, 10.0, 0.44, 0.55, 0.62])
+    ens = isg.Ensemble(Ls, seeds, models=models, delta=1.9, record_capacity=4)
+    ens.init_random()
+    ens.sweep(len(betas), betas=betas, record_every=5)
+    rows = ens.read_records()
+    for r, (L, m, sd) in enumerate(zip(Ls, models, seeds)):
+        recs, s = _alone(isg, L, m, sd, betas, 5, delta=1.9)
+        for k, rec in enumerate(recs):
+            _same_obs(rows[k][r], rec)
+        assert np.array_equal(ens.get(r), s), (L, m)
+    ens.close()
+
+
 def test_many_global_path_launches_run_without_a_graph(isg):
     """Replicas too large for shared memory (Blume-Capel L = 1024) cost one
     launch per half-sweep; a call with more than 2^16 of them is queued on
