@@ -87,6 +87,7 @@ struct isg_ensemble {
         int64_t L;
         std::vector<uint32_t *> planes;
         std::vector<uint64_t> seeds;
+        std::vector<int64_t> reps;  // replica indices
     };
     std::vector<GlobalGroup> groups;
     int32_t *d_counter = nullptr;
@@ -201,10 +202,13 @@ isg_status queue_sweeps(isg_ensemble *e, int64_t n, int64_t record_every, int64_
                       "half-sweep launch");
         if (record_every > 0 && (i + 1) % record_every == 0) {
             const int64_t row = (rec_row0 + (i + 1) / record_every - 1) % e->rec_cap;
-            for (int64_t r : e->global_list) {
-                uint8_t *rec = e->rec_ring + (uint64_t)row * e->row_bytes + e->rec_off[r];
-                ECUDA(cudaMemsetAsync(rec, 0, record_stride(e->L[r]), st), "record clear");
-                ECUDA(launch_measure(replica_planes(e, r), rec, (int64_t)t + 1, st), "measure launch");
+            for (const auto &gr : e->groups) {
+                std::vector<uint8_t *> recs(gr.reps.size());
+                for (size_t k = 0; k < gr.reps.size(); ++k)
+                    recs[k] = e->rec_ring + (uint64_t)row * e->row_bytes + e->rec_off[gr.reps[k]];
+                ECUDA(launch_measure_multi(gr.model, gr.L, gr.planes.data(), recs.data(),
+                                           (int)gr.planes.size(), (int64_t)t + 1, st),
+                      "measure launch");
             }
         }
     }
@@ -303,11 +307,12 @@ isg_status isg_ensemble_create(const isg_ensemble_desc *d, isg_ensemble **out)
             return gr.model == e->model[r] && gr.L == e->L[r];
         });
         if (it == e->groups.end()) {
-            e->groups.push_back({e->model[r], e->L[r], {}, {}});
+            e->groups.push_back({e->model[r], e->L[r], {}, {}, {}});
             it = e->groups.end() - 1;
         }
         it->planes.push_back(reinterpret_cast<uint32_t *>(e->planes + e->plane_off[r]));
         it->seeds.push_back(e->seed[r]);
+        it->reps.push_back(r);
     }
     // lattices that fit half the largest shared-memory request run on
     // half-CTA teams (isg_batch.cuh); the request covers two of them
@@ -430,8 +435,9 @@ isg_status isg_ensemble_sweep(isg_ensemble *e, int64_t n, const double *betas, d
     for (const auto &gr : e->groups)
         multi_per_sweep += 2 * (((int64_t)gr.planes.size() + kMultiMax - 1) / kMultiMax);
     const int64_t multi_launches = multi_per_sweep * n;
-    const int64_t global_launches =
-        multi_launches + (int64_t)e->global_list.size() * (record_every > 0 ? n / record_every : 0);
+    int64_t global_launches = multi_launches;
+    if (record_every > 0)
+        global_launches += (multi_per_sweep) * (n / record_every);  // zeroing + measure per group chunk
     if (global_launches > kMaxGraphLaunches || multi_launches > kMaxGraphMultiLaunches) {
         ECUDA(cudaMemcpyAsync(e->d_ithr, e->h_ithr, sizeof(IsingThr) * n, cudaMemcpyHostToDevice, st),
               "threshold upload");

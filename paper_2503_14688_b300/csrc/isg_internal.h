@@ -100,6 +100,10 @@ cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaSt
 // parameters allow (kMultiMax lattices each); same results as n single
 // launches.
 constexpr int kMultiMax = 240;  // lattices per launch: 240 x 100 B of parameters
+// Records (zeroed here first) of n lattices of one model and side L after
+// sweep `sweep`, in as few launches as the kernel parameters allow.
+cudaError_t launch_measure_multi(int model, int64_t L, uint32_t *const *planes, uint8_t *const *recs, int n,
+                                 int64_t sweep, cudaStream_t st);
 cudaError_t launch_half_sweep_multi(int model, int64_t L, uint32_t *const *planes, const uint64_t *seeds,
                                     int n, uint32_t t, int colour, const IsingThr &ithr,
                                     const BcTable *btab, cudaStream_t st);

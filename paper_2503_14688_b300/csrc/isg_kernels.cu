@@ -425,11 +425,10 @@ __device__ __forceinline__ void cc_zero(ColumnCounter &k)
 }
 
 template <int MODEL>
-__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
-    k_measure(Planes pl, int H, int64_t *__restrict__ rec_hdr, int32_t *__restrict__ R,
-              int32_t *__restrict__ C, int64_t sweep)
+__device__ __forceinline__ void measure_band(const Planes &pl, int H, int64_t *__restrict__ rec_hdr,
+                                             int32_t *__restrict__ R, int32_t *__restrict__ C,
+                                             int64_t sweep, int32_t *s_row)
 {
-    __shared__ int32_t s_row[kMeasureBand];
     const int64_t L = pl.L, W = pl.W, LW = L * W;
     const int64_t y0 = (int64_t)blockIdx.y * H;
     const int rows = (int)((y0 + H < L ? y0 + H : L) - y0);  // a multiple of 16
@@ -586,6 +585,49 @@ __global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
     for (int i = threadIdx.x; i < rows; i += blockDim.x)
         if (s_row[i])
             atomicAdd(&R[y0 + i], s_row[i]);
+}
+
+template <int MODEL>
+__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
+    k_measure(Planes pl, int H, int64_t *__restrict__ rec_hdr, int32_t *__restrict__ R,
+              int32_t *__restrict__ C, int64_t sweep)
+{
+    __shared__ int32_t s_row[kMeasureBand];
+    measure_band<MODEL>(pl, H, rec_hdr, R, C, sweep, s_row);
+}
+
+// Records of many lattices of one side L in one launch (the ensemble's
+// replicas too large for shared memory): lattice blockIdx.z, its planes and
+// its record slot (zeroed beforehand) in the kernel parameters.
+struct MeasureMultiArgs {
+    uint32_t *planes[kMultiMax];
+    uint8_t *rec[kMultiMax];
+};
+
+template <int MODEL>
+__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
+    k_measure_multi(int64_t L, int H, int64_t sweep, const __grid_constant__ MeasureMultiArgs a)
+{
+    __shared__ int32_t s_row[kMeasureBand];
+    const int r = blockIdx.z;
+    Planes pl;
+    pl.base = a.planes[r];
+    pl.L = L;
+    pl.W = L / 64;
+    pl.model = MODEL;
+    int64_t *hdr = reinterpret_cast<int64_t *>(a.rec[r]);
+    int32_t *R = reinterpret_cast<int32_t *>(hdr + 4);
+    measure_band<MODEL>(pl, H, hdr, R, R + L, sweep, s_row);
+}
+
+// Zero the record slots of a multi-lattice measure launch.
+__global__ void k_zero_records(const __grid_constant__ MeasureMultiArgs a, int n, uint32_t words)
+{
+    for (int r = blockIdx.y; r < n; r += gridDim.y) {
+        uint32_t *p = reinterpret_cast<uint32_t *>(a.rec[r]);
+        for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x)
+            p[i] = 0u;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -901,6 +943,37 @@ cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaSt
     else
         k_measure<1><<<grid, kMeasureThreads, 0, st>>>(pl, (int)H, hdr, R, C, sweep);
     return cudaGetLastError();
+}
+
+cudaError_t launch_measure_multi(int model, int64_t L, uint32_t *const *planes, uint8_t *const *recs, int n,
+                                 int64_t sweep, cudaStream_t st)
+{
+    const int64_t W = L / 64;
+    const int64_t bx = (W + kMeasureThreads - 1) / kMeasureThreads;
+    for (int i0 = 0; i0 < n; i0 += kMultiMax) {
+        const int m = n - i0 < kMultiMax ? n - i0 : kMultiMax;
+        MeasureMultiArgs a;
+        for (int i = 0; i < m; ++i) {
+            a.planes[i] = planes[i0 + i];
+            a.rec[i] = recs[i0 + i];
+        }
+        const uint32_t words = (uint32_t)(record_stride(L) / 4);
+        k_zero_records<<<dim3((words + 255) / 256, (unsigned)m), 256, 0, st>>>(a, m, words);
+        // band height as for one lattice, taller while the m lattices keep
+        // a few blocks per SM (fewer column atomics)
+        int64_t H = L < kMeasureBand ? L : kMeasureBand;
+        while (H % 32 == 0 && bx * ((L + H - 1) / H) * m < 148 * 4)
+            H >>= 1;
+        const dim3 grid((unsigned)bx, (unsigned)((L + H - 1) / H), (unsigned)m);
+        if (model == 0)
+            k_measure_multi<0><<<grid, kMeasureThreads, 0, st>>>(L, (int)H, sweep, a);
+        else
+            k_measure_multi<1><<<grid, kMeasureThreads, 0, st>>>(L, (int)H, sweep, a);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
 }
 
 cudaError_t launch_correlation(const Planes &pl, int nr, const int64_t *d_r, unsigned long long *d_out,
