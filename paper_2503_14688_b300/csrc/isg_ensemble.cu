@@ -428,16 +428,17 @@ isg_status isg_ensemble_sweep(isg_ensemble *e, int64_t n, const double *betas, d
     }
     const int64_t row0 = (e->rec_head + e->rec_count) % e->rec_cap;
     cudaStream_t st = e->stream;
-    // replicas too large for shared memory cost one launch per half-sweep
-    // (and record); beyond kMaxGraphLaunches the graph's host memory would
-    // grow without bound, so such a call is queued on the stream directly
+    // replicas too large for shared memory cost one multi-lattice launch per
+    // group and half-sweep (two per group and record: zeroing, measure);
+    // beyond the limits the graph's host memory would grow with the call's
+    // length, so such a call is queued on the stream directly
     int64_t multi_per_sweep = 0;
     for (const auto &gr : e->groups)
         multi_per_sweep += 2 * (((int64_t)gr.planes.size() + kMultiMax - 1) / kMultiMax);
     const int64_t multi_launches = multi_per_sweep * n;
     int64_t global_launches = multi_launches;
     if (record_every > 0)
-        global_launches += (multi_per_sweep) * (n / record_every);  // zeroing + measure per group chunk
+        global_launches += multi_per_sweep * (n / record_every);  // zeroing + measure per group chunk
     if (global_launches > kMaxGraphLaunches || multi_launches > kMaxGraphMultiLaunches) {
         ECUDA(cudaMemcpyAsync(e->d_ithr, e->h_ithr, sizeof(IsingThr) * n, cudaMemcpyHostToDevice, st),
               "threshold upload");
