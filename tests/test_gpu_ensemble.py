@@ -114,22 +114,25 @@ def test_multi_lattice_launches_with_odd_word_counts(isg):
     ens.close()
 
 
-def test_many_global_path_launches_run_without_a_graph(isg):
-    """Replicas too large for shared memory (Blume-Capel L = 1024) cost one
-    launch per half-sweep; a call with more than 2^16 of them is queued on
-    the stream instead of captured.  Its replicas equal lattices alone."""
-    n_rep, n = 36, 1000  # 36 x (2 x 1000 + 100 records) launches
+def test_long_call_over_large_replicas_runs_without_a_graph(isg):
+    """Replicas too large for shared memory (Blume-Capel L = 1024) take one
+    multi-lattice launch per half-sweep; a call with more than 2048 of them
+    is queued on the stream instead of captured.  Its replicas and records
+    equal lattices alone, and a following short (captured) call continues
+    them."""
+    n_rep, n = 8, 1100  # 2 x 1100 multi-lattice launches
     Ls = [1024] * n_rep
     seeds = [wl.BASE_SEED + 700 + r for r in range(n_rep)]
-    betas = np.full(n, 1 / wl.T_C_BLUME_CAPEL)
-    ens = isg.Ensemble(Ls, seeds, models=[1] * n_rep, delta=0.0, record_capacity=101)
+    betas = np.full(n + 20, 1 / wl.T_C_BLUME_CAPEL)
+    ens = isg.Ensemble(Ls, seeds, models=[1] * n_rep, delta=0.0, record_capacity=120)
     ens.init_random()
-    ens.sweep(n, betas=betas, record_every=10)
+    ens.sweep(n, betas=betas[:n], record_every=10)
+    ens.sweep(20, betas=betas[n:], record_every=10)
     rows = ens.read_records()
-    assert len(rows) == 100
-    for r in (0, 17, 35):
+    assert len(rows) == 112
+    for r in (0, 5):
         recs, s = _alone(isg, 1024, 1, seeds[r], betas, 10)
-        for k in (0, 49, 99):
+        for k in (0, 55, 109, 110, 111):
             _same_obs(rows[k][r], recs[k])
         assert np.array_equal(ens.get(r), s)
     ens.close()
