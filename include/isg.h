@@ -241,7 +241,8 @@ double isg_xi2(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const i
  * in shared memory (Ising L <= 1280, Blume-Capel L <= 896) are run by one
  * persistent kernel -- each CTA takes whole replicas from a work counter,
  * largest first, and keeps them in shared memory for all sweeps of a call;
- * larger replicas are swept by the single-lattice kernels on the same stream.
+ * larger replicas are grouped by (model, L) and each group is swept by
+ * multi-lattice launches (up to 240 lattices each) on the same stream.
  * Replica r evolves bit for bit like a lattice created alone with seed[r].
  * ------------------------------------------------------------------------- */
 typedef struct isg_ensemble isg_ensemble;
@@ -272,7 +273,9 @@ isg_status isg_ensemble_init_random(isg_ensemble *ens);
  * (ISG_ERR_BUSY if the ring lacks room).  The device work of the call (the
  * threshold upload, one persistent launch, the large replicas' launches) is
  * captured in a CUDA graph, instantiated once and updated in place by later
- * calls of the same shape.  Asynchronous. */
+ * calls of the same shape; a call whose large replicas need more than 2^16
+ * launches (2048 multi-lattice ones) is queued on the stream directly
+ * instead.  Asynchronous. */
 isg_status isg_ensemble_sweep(isg_ensemble *ens, int64_t n, const double *betas,
                               double beta_const, int64_t record_every);
 
@@ -303,7 +306,7 @@ isg_status isg_ensemble_autotune(isg_ensemble *ens, int64_t sweeps, int32_t *thr
  * requests, admits arrived requests in arrival order while the device-memory
  * budget and the slot count allow, and advances every running request by
  * chunk_sweeps sweeps -- lattices that fit in shared memory (Ising L <= 1280,
- * Blume-Capel L <= 768) together in one persistent launch, larger ones on
+ * Blume-Capel L <= 896) together in one persistent launch, larger ones on
  * streams of their own, overlapping it.  A result does not depend on what
  * else ran or where chunks were cut (per-site keying).
  * ------------------------------------------------------------------------- */
