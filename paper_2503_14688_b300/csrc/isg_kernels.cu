@@ -852,21 +852,35 @@ cudaError_t launch_init_uniform(const Planes &pl, int value, cudaStream_t st)
     return cudaGetLastError();
 }
 
+// Words per thread: the most that still gives `waves` full waves of
+// resident blocks with one-row bands, and that divides the row.  A lattice
+// of a few thousand rows has too few threads at four words per thread:
+// Ising L = 2048 runs at 511 instead of 341 flips/ns with one word per
+// thread, L = 4096 at 837 instead of 819; from L = 8192 on four words win
+// (1261 against 1171 with one).
+int words_per_thread(int64_t L, int64_t W, int vmax, int blocks_per_sm, int threads, int waves)
+{
+    for (int V = vmax; V > 1; V >>= 1)
+        if (W % V == 0 && (W / V) * L >= 148LL * blocks_per_sm * threads * waves)
+            return V;
+    return 1;
+}
+
 cudaError_t launch_half_sweep(const Planes &pl, int colour, const PhiloxLaunch &ph,
                               const IsingThr &ithr, const BcTable *btab, cudaStream_t st)
 {
-    const int V = (pl.W % 4 == 0) ? 4 : (pl.W % 2 == 0 ? 2 : 1);
     if (pl.model == 0) {
+        const int V = words_per_thread(pl.L, pl.W, 4, kSweepMinBlocks, kSweepThreads, 1);
         if (V == 4)
             return launch_ising<4>(pl, colour, ph, ithr, st);
         if (V == 2)
             return launch_ising<2>(pl, colour, ph, ithr, st);
         return launch_ising<1>(pl, colour, ph, ithr, st);
     }
-    // Blume-Capel: two words per thread (more threads in flight than four
-    // at the same 80 registers: 137 vs 148 ms per half-sweep at L = 2^19,
-    // 919 vs 898 flips/ns at L = 16384)
-    if (V >= 2)
+    // Blume-Capel: at most two words per thread (more threads in flight than
+    // four at the same 80 registers: 137 vs 148 ms per half-sweep at
+    // L = 2^19, 919 vs 898 flips/ns at L = 16384)
+    if (words_per_thread(pl.L, pl.W, 2, kBcMinBlocks, kBcThreads, 1) == 2)
         return launch_bc<2>(pl, colour, ph, *btab, st);
     return launch_bc<1>(pl, colour, ph, *btab, st);
 }
