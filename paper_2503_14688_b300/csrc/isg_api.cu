@@ -8,6 +8,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <limits>
 #include <new>
 #include <vector>
 
@@ -86,6 +87,10 @@ struct isg_lattice {
     int device;
     uint32_t *sw_labels = nullptr;  // Swendsen-Wang labels (allocated on first use)
     int64_t sw_count = 0;           // Swendsen-Wang iterations done
+    // thresholds of the last beta a half-sweep used (NaN: none yet)
+    double thr_beta = std::numeric_limits<double>::quiet_NaN();
+    IsingThr thr_ising{};
+    BcTable thr_bc{};
 };
 
 namespace {
@@ -116,16 +121,16 @@ isg_status queue_half(isg_lattice *lat, int colour, double beta)
 {
     PhiloxLaunch ph;
     philox_launch_consts(lat->seed, (uint32_t)lat->t, (uint32_t)colour, &ph);
-    IsingThr ithr{};
-    BcTable tab;
-    const BcTable *tp = nullptr;
-    if (lat->model == ISG_ISING) {
-        ising_thresholds(beta, &ithr);
-    } else {
-        bc_table(beta, lat->delta, &tab);
-        tp = &tab;
+    if (!(beta == lat->thr_beta)) {  // both colours and constant-beta runs reuse the table
+        if (lat->model == ISG_ISING)
+            ising_thresholds(beta, &lat->thr_ising);
+        else
+            bc_table(beta, lat->delta, &lat->thr_bc);
+        lat->thr_beta = beta;
     }
-    ISG_CUDA(launch_half_sweep(planes_of(lat), colour, ph, ithr, tp, lat->stream), "half-sweep launch");
+    const BcTable *tp = lat->model == ISG_ISING ? nullptr : &lat->thr_bc;
+    ISG_CUDA(launch_half_sweep(planes_of(lat), colour, ph, lat->thr_ising, tp, lat->stream),
+             "half-sweep launch");
     if (colour == 1)
         lat->t += 1;
     return ISG_OK;
