@@ -472,14 +472,14 @@ __device__ __forceinline__ void measure_band(const Planes &pl, int H, int64_t *_
     const uint32_t *p0c = p0 + wc, *p1c = p1 + wc;
     const uint32_t *n0c = n0 + wc, *n1c = n1 + wc;
     const int64_t off_l = wl - wc, off_r = wr - wc;
+    const uint32_t *t1 = p1c + y0 * W, *t0 = p0c + y0 * W;  // row y0 + r0 + 4 g, advanced by 4 rows
     for (int r0 = 0; r0 < rows; r0 += 16) {
 #pragma unroll 1
-        for (int g = 0; g < 4; ++g) {
+        for (int g = 0; g < 4; ++g, t1 += 4 * W, t0 += 4 * W) {
             const int64_t yg = y0 + r0 + 4 * g;
             const bool last = yg + 4 == L;  // row yg + 3 wraps to row 0
             uint32_t Tp[4], Dp[4], Ep[4], Tn[4], Dn[4], En[4];
             if (active) {
-                const uint32_t *t1 = p1c + yg * W, *t0 = p0c + yg * W;
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const uint32_t *down = (r == 3 && last) ? p0c : t0 + (r + 1) * W;
