@@ -272,30 +272,37 @@ __device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ t
                                              int64_t W, int colour, int H, const PhiloxLaunch &pc,
                                              const uint32_t *s_thr, const uint32_t *s_nib)
 {
-    const int64_t tpr = W / V;
-    const int64_t band = g / tpr;
-    const int64_t w0 = (g - band * tpr) * V;
-    const int64_t y0 = band * H;
-    if (y0 >= L)
+    // rows and words fit 32 bits; row pointers advance by one row per step
+    const uint32_t Li = (uint32_t)L, Wi = (uint32_t)W;
+    const uint32_t tpr = Wi / V;
+    const uint32_t band = (uint32_t)(g / tpr);
+    const uint32_t w0 = ((uint32_t)g - band * tpr) * V;
+    const uint32_t y0 = band * (uint32_t)H;
+    if (y0 >= Li)
         return;
-    const int64_t y1 = y0 + H < L ? y0 + H : L;
-    const uint64_t qrow = (uint64_t)(L / 8);
-    const int64_t yu0 = y0 == 0 ? L - 1 : y0 - 1;
+    const uint32_t y1 = y0 + H < Li ? y0 + H : Li;
+    const uint64_t qrow = (uint64_t)(Li / 8);
+    const uint32_t yu0 = y0 == 0 ? Li - 1 : y0 - 1;
+    const uint32_t e_left = w0 == 0 ? Wi - 1 : w0 - 1;
+    const uint32_t e_right = w0 + V == Wi ? 0 : w0 + V;
+    const int64_t dpn = np_plane - nn_plane, dtp = tp_plane - tn_plane;  // occupancy -> sign plane
 
-    Words<V> Un = load_words<V>(nn_plane + yu0 * W + w0);
-    Words<V> Up = load_words<V>(np_plane + yu0 * W + w0);
-    Words<V> Sn = load_words<V>(nn_plane + y0 * W + w0);
-    Words<V> Sp = load_words<V>(np_plane + y0 * W + w0);
-    for (int64_t y = y0; y < y1; ++y) {
-        const int64_t yd = y + 1 == L ? 0 : y + 1;
-        const Words<V> Dn = load_words<V>(nn_plane + yd * W + w0);
-        const Words<V> Dp = load_words<V>(np_plane + yd * W + w0);
+    Words<V> Un = load_words<V>(nn_plane + (uint64_t)yu0 * Wi + w0);
+    Words<V> Up = load_words<V>(np_plane + (uint64_t)yu0 * Wi + w0);
+    const uint32_t *nrow = nn_plane + (uint64_t)y0 * Wi;
+    uint32_t *trow = tn_plane + (uint64_t)y0 * Wi;
+    Words<V> Sn = load_words<V>(nrow + w0);
+    Words<V> Sp = load_words<V>(nrow + dpn + w0);
+    for (uint32_t y = y0; y < y1; ++y) {
+        const uint32_t *ndown = y + 1 == Li ? nn_plane : nrow + Wi;
+        const Words<V> Dn = load_words<V>(ndown + w0);
+        const Words<V> Dp = load_words<V>(ndown + dpn + w0);
         const int parity = (colour ^ (int)y) & 1;
-        const int64_t ew = y * W + edge_word(w0, V, W, parity);
-        const Words<V> Xn = side_words<V>(Sn, __ldg(nn_plane + ew), parity);
-        const Words<V> Xp = side_words<V>(Sp, __ldg(np_plane + ew), parity);
-        Words<V> Tn = load_words_rw<V>(tn_plane + y * W + w0);
-        Words<V> Tp = load_words_rw<V>(tp_plane + y * W + w0);
+        const uint32_t *edge = nrow + (parity == 0 ? e_left : e_right);
+        const Words<V> Xn = side_words<V>(Sn, __ldg(edge), parity);
+        const Words<V> Xp = side_words<V>(Sp, __ldg(edge + dpn), parity);
+        Words<V> Tn = load_words_rw<V>(trow + w0);
+        Words<V> Tp = load_words_rw<V>(trow + dtp + w0);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
             const uint32_t nbn[4] = {Un.v[v], Dn.v[v], Sn.v[v], Xn.v[v]};
@@ -303,12 +310,14 @@ __device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ t
             const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)(w0 + v);
             bc_word_update<kFull>(Tn.v[v], Tp.v[v], nbn, nbp, q0, pc, s_thr, s_nib);
         }
-        store_words<V>(tn_plane + y * W + w0, Tn);
-        store_words<V>(tp_plane + y * W + w0, Tp);
+        store_words<V>(trow + w0, Tn);
+        store_words<V>(trow + dtp + w0, Tp);
         Un = Sn;
         Up = Sp;
         Sn = Dn;
         Sp = Dp;
+        nrow += Wi;
+        trow += Wi;
     }
 }
 
