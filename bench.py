@@ -58,11 +58,11 @@ WIDE_MUL_PER_SM_CLK = 32
 WIDE_MUL_PER_SITE = 18 / 4
 # DRAM bytes (read + write) per site of one half-sweep launch, from one ncu
 # capture of the current kernels on a smaller lattice (Ising L = 2^16:
-# 536.9 + 229.4 MB per 2^31 sites; Blume-Capel L = 2^15: 274.5 + 93.2 MB per
+# 536.9 + 229.4 MB per 2^31 sites; Blume-Capel L = 2^15: 274.3 + 93.5 MB per
 # 2^29 sites), scaled to a full launch by the sites it updates.  Against the
 # algorithmic 0.375 (Ising) and 0.75 (Blume-Capel) B per site.
 DRAM_BYTES_PER_SITE = {wl.ISING: (536.9e6 + 229.4e6) / 2**31,
-                       wl.BLUME_CAPEL: (274.5e6 + 93.2e6) / 2**29}
+                       wl.BLUME_CAPEL: (274.3e6 + 93.5e6) / 2**29}
 
 
 def _l2_note(lattice_bytes):
