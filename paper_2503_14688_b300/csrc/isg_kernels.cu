@@ -682,8 +682,9 @@ __global__ void __launch_bounds__(kMeasureThreads)
         const int cp = c ^ (int)(r & 1);
         int ax = 0, ay = 0;
         if (active && MODEL == 0) {
-            // horizontal partner of row parity q = (c ^ y) & 1: bits i + kk of
-            // the same row of plane cp, i.e. two words w1, w2 shifted by sh
+            // Ising (the MODEL == 1 terms below compile away).  Horizontal
+            // partner of row parity q = (c ^ y) & 1: bits i + kk of the same
+            // row of plane cp, i.e. two words w1, w2 shifted by sh
             auto split = [&](int q, int64_t &a, int64_t &b, unsigned &sh) {
                 int64_t kk = (r & 1) ? (r - 1) / 2 + q : r / 2;
                 if (kk >= half)
