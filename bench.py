@@ -9,15 +9,24 @@ logged every 10 sweeps), every sweep for the small workloads; the line also
 reports the step recording every sweep.  The default workload is the single
 large Ising lattice, L = 2^20 (2^40 spins, 128 GiB of bit-planes), hot start,
 quench to beta_c; the lattice is far larger than L2, so no flush is needed
-between steps.
+between steps.  The line carries the other large-quench lattice, Blume-Capel
+Delta = 0 at L = 2^19 (64 GiB), measured the same way (`blume_capel_large`),
+the replica ensemble (`batched`), the served request stream (`served`), the
+pre-cooling scan, Swendsen-Wang and the oracle on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload ising_large|blume_capel_large|ising_small|blume_capel_parity]
+                    [--served-requests N] [--served-saturated N]
+                    [--no-bc] [--no-batched] [--no-served] [--no-precool] [--no-sw]
+                    [--no-cpu-baseline] [--no-calib]
 
 Prints one JSON line.  `value` is the device-timed throughput (spin-flip
 attempts per ns, all ranks); `e2e` is the same metric through the public C
 ABI with host inputs (the beta of each sweep) and host outputs (each sweep's
 record read back, xi_2 computed on the host) inside the timed region.
+`roofline.frac` is the dominant half-sweep against the integer-issue peak
+(SM count read from the device); `roofline.pipe_bound` is the same launch
+against a per-pipe bound from integer rates measured at the start of the run.
 With --impl reference the oracle (CPU) is timed on a bounded sample.
 """
 import argparse
@@ -49,18 +58,16 @@ UNIT = "flips/ns"
 #   Blume-Capel: the same Philox plus the spin-1 acceptance (about six
 #   compares over the candidate energies) and the two-plane update: about 25.
 ALG_OPS_PER_SITE = {wl.ISING: 15.0, wl.BLUME_CAPEL: 25.0}
-SMS = 148
 INT_LANES_PER_SM = 128     # 4 SMSPs x 32 lanes, one warp-instruction per SMSP per clock
-# The pipe that binds the half-sweep: the 32x32->64 multiplies of Philox run
-# on the FMA-heavy pipe at 32 per SM per clock (calibrated on a B300, half
-# the rate of a 32-bit multiply-add); the sweep needs 18 per 4 sites.
-WIDE_MUL_PER_SM_CLK = 32
-WIDE_MUL_PER_SITE = 18 / 4
-# DRAM bytes (read + write) per site of one half-sweep launch, from one ncu
-# capture of the current kernels on a smaller lattice (Ising L = 2^16:
-# 536.9 + 229.4 MB per 2^31 sites; Blume-Capel L = 2^15: 274.3 + 93.5 MB per
-# 2^29 sites), scaled to a full launch by the sites it updates.  Against the
-# algorithmic 0.375 (Ising) and 0.75 (Blume-Capel) B per site.
+# The same algorithmic counts split by execution pipe (pipe-aware bound):
+# Philox's 5 wide (32x32->64) multiplies per site run on the FMA-heavy pipe,
+# its 5 three-input XORs on the ALU pipe, and the remaining ops (Ising 5,
+# Blume-Capel 15) may issue on either pipe.
+PIPE_OPS = {wl.ISING: {"wide": 5.0, "alu": 5.0, "either": 5.0},
+            wl.BLUME_CAPEL: {"wide": 5.0, "alu": 5.0, "either": 15.0}}
+# The kernels fold the launch-uniform parts of Philox's first two rounds:
+# 18 wide multiplies per 4 sites instead of 20.
+WIDE_MUL_PER_SITE_FOLDED = 18 / 4
 DRAM_BYTES_PER_SITE = {wl.ISING: (536.9e6 + 229.4e6) / 2**31,
                        wl.BLUME_CAPEL: (274.3e6 + 93.5e6) / 2**29}
 
@@ -201,12 +208,29 @@ def batched_bench(sweeps=10000, n_rep=4096, record_every=1000):
     torch.cuda.synchronize()
     single = float(Ls1) ** 2 * n1 / (a.elapsed_time(b) * 1e6)
     lat.close()
+    # the same replicas swept one lattice at a time through the single-lattice
+    # path (sweeps_alone sweeps each, one after another on one stream)
+    sweeps_alone = 100
+    lats = [P.Lattice(int(L), wl.ISING, seed=s_, stream=stream) for L, s_ in zip(Ls, seeds)]
+    for x in lats:
+        x.init_random()
+    torch.cuda.synchronize()
+    a.record(stream)
+    for x in lats:
+        x.sweep(sweeps_alone, beta=wl.BETA_C_ISING)
+    b.record(stream)
+    torch.cuda.synchronize()
+    one_at_a_time = spins * sweeps_alone / (a.elapsed_time(b) * 1e6)
+    for x in lats:
+        x.close()
     return {"workload": f"{n_rep} Ising replicas, L uniform in {{64..1024}}, beta_c, "
                         f"{sweeps} sweeps in one persistent launch, records every {record_every}",
             "value": batched, "unit": UNIT, "ms": ms, "spins": spins, "record_rows": len(rows),
             "threads_per_cta": threads,
             "single_lattice_equal_spins": {"L": Ls1, "value": single, "unit": UNIT},
-            "ratio_vs_single": batched / single}
+            "ratio_vs_single": batched / single,
+            "one_lattice_at_a_time": {"sweeps": sweeps_alone, "value": one_at_a_time,
+                                      "unit": UNIT, "batched_speedup": batched / one_at_a_time}}
 
 
 def precool_bench(n_rep=4096):
@@ -267,22 +291,25 @@ def sw_bench(Ls=(4096, 16384), reps=20):
             "bytes_per_site": 24.75, "sizes": out}
 
 
-def served_bench(n_req=48, load=0.9, chunk=100, max_active=48):
+def served_bench(n_req=2000, n_saturated=200, load=0.9, chunk=100, max_active=48):
     """The served stream: requests of the served workload (workloads.py)
-    through the continuous-batching server.  First all at once (capacity and
-    makespan), then with Poisson arrivals at `load` x that capacity (p50/p99
-    latency from arrival to completion, aggregate throughput)."""
+    through the continuous-batching server.  Capacity: the stream's first
+    `n_saturated` requests submitted at once (saturated throughput and its
+    ratio to the same mix run as single lattices).  Latency: all `n_req`
+    requests with Poisson arrivals at `load` x that capacity -- p50/p99 of
+    arrival-to-completion, and of the slowdown (latency over the request's
+    time alone at the single-lattice rate of its model); under processor
+    sharing the mean slowdown at load rho is 1 / (1 - rho)."""
     import paper_2503_14688_b300 as P
 
     reqs = wl.served_requests(n_req)
-    flips = [r["L"] ** 2 * r["sweeps"] for r in reqs]
-    total = float(sum(flips))
+    flips = np.array([float(r["L"]) ** 2 * r["sweeps"] for r in reqs])
     budget = 96 << 30
 
-    def run(arrivals):
+    def run(sub, arrivals):
         srv = P.Server(hbm_budget=budget, max_active=max_active, chunk_sweeps=chunk)
         ids = []
-        for r, a in zip(reqs, arrivals):
+        for r, a in zip(sub, arrivals):
             ids.append(srv.submit(r["model"], r["L"], r["seed"], r["sweeps"], r["t_start"],
                                   r["beta"], arrival_time=a))
         srv.drain()
@@ -311,25 +338,36 @@ def served_bench(n_req=48, load=0.9, chunk=100, max_active=48):
         torch.cuda.synchronize()
         ref_rate[model] = 32768.0 ** 2 * 50 / (a.elapsed_time(b) * 1e-3)
         lat.close()
-    ref = total / sum(f / ref_rate[r["model"]] for f, r in zip(flips, reqs))
+    alone = np.array([f / ref_rate[r["model"]] for f, r in zip(flips, reqs)])  # s at full rate
 
-    lat0, span0 = run([0.0] * n_req)
-    capacity = total / span0  # flips/s with the queue always full
+    sat = reqs[:n_saturated]
+    sat_total = float(flips[:n_saturated].sum())
+    ref = sat_total / float(alone[:n_saturated].sum())
+    _, span0 = run(sat, [0.0] * len(sat))
+    capacity = sat_total / span0  # flips/s with the queue always full
+    total = float(flips.sum())
     rate = load * capacity / (total / n_req)
     arrivals = wl.poisson_arrivals(n_req, rate)
-    lat, span = run(list(arrivals))
+    lat, span = run(reqs, list(arrivals))
+    slow = lat / alone
     return {"workload": f"{n_req} requests: Ising or Blume-Capel (p=1/2), L=2^k, k in 8..14, "
                         f"sweeps log-uniform in [1e3, 1e4], 10-step bath 1.5 T_c -> 1.01 T_c; "
                         f"chunk {chunk} sweeps, {max_active} slots",
-            "saturated": {"value": capacity / 1e9, "unit": UNIT, "makespan_s": span0,
+            "saturated": {"requests": len(sat), "value": capacity / 1e9, "unit": UNIT,
+                          "makespan_s": span0, "flips": sat_total,
                           "single_lattice_mix": {"value": ref / 1e9, "unit": UNIT,
                                                  "ising_L32768": ref_rate[wl.ISING] / 1e9,
                                                  "blume_capel_L32768":
                                                      ref_rate[wl.BLUME_CAPEL] / 1e9},
                           "ratio_vs_single": capacity / ref},
-            "poisson": {"load": load, "rate_per_s": rate, "value": total / span / 1e9,
-                        "unit": UNIT, "p50_s": float(np.percentile(lat, 50)),
-                        "p99_s": float(np.percentile(lat, 99)), "makespan_s": span},
+            "poisson": {"requests": n_req, "load": load, "rate_per_s": rate,
+                        "value": total / span / 1e9, "unit": UNIT,
+                        "p50_s": float(np.percentile(lat, 50)),
+                        "p99_s": float(np.percentile(lat, 99)), "makespan_s": span,
+                        "slowdown_p50": float(np.percentile(slow, 50)),
+                        "slowdown_p99": float(np.percentile(slow, 99)),
+                        "slowdown_mean": float(slow.mean()),
+                        "slowdown_processor_sharing": 1.0 / (1.0 - load)},
             "total_flips": total}
 
 
@@ -366,23 +404,63 @@ def run_reference(args, w):
     print(json.dumps(line), flush=True)
 
 
-def run_ours(args, w):
+def roofline(model, sites, dom_ms, which, half_ms, sms, sm_max, peak_src, rates):
+    """The dominant half-sweep launch against the integer-issue peak (the
+    headline `frac`) and against the pipe-aware bound from the rates measured
+    in this run (`pipe_bound`)."""
+    peak = sms * INT_LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s
+    per_launch = sites / 2
+    achieved = ALG_OPS_PER_SITE[model] * per_launch / (dom_ms * 1e-3) / 1e12
+    sites_per_ns = per_launch / (dom_ms * 1e6)
+    out = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+           "frac": achieved / peak,
+           "traffic": DRAM_BYTES_PER_SITE[model] * per_launch,
+           "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of one half-sweep at "
+                            "L=2^16 (Ising) / 2^15 (Blume-Capel), scaled by sites per launch; "
+                            f"algorithmic {0.375 if model == wl.ISING else 0.75} B/site",
+           "kernel": "half-sweep colour %d" % which,
+           "ops_per_site": ALG_OPS_PER_SITE[model],
+           "peak_basis": f"{sms} SMs (device) x {INT_LANES_PER_SM} int lanes x {sm_max:.0f} MHz "
+                         f"({peak_src})",
+           "half_sweep_ms": half_ms,
+           "achieved_sites_per_ns": sites_per_ns}
+    if rates:
+        rw = rates["wide_multiply"]["per_sm_per_clk"]
+        ra = rates["alu_op"]["per_sm_per_clk"]
+        ops = PIPE_OPS[model]
+        t_fma = ops["wide"] / rw
+        t_alu = ops["alu"] / ra
+        t_all = (ops["wide"] / rw + (ops["alu"] + ops["either"]) / ra) / 2
+        t = max(t_fma, t_alu, t_all)
+        bound = sms * sm_max * 1e6 / t / 1e9
+        wide_bound = sms * sm_max * 1e6 * rw / ops["wide"] / 1e9
+        folded = sms * sm_max * 1e6 * rw / WIDE_MUL_PER_SITE_FOLDED / 1e9
+        out["pipe_bound"] = {
+            "basis": "per site: max(wide/r_wide, alu/r_alu, (wide/r_wide + (alu + either)/r_alu)/2) "
+                     "SM-clocks with the algorithmic counts and the rates measured in this run",
+            "ops_per_site": ops, "rates_per_sm_per_clk": {"wide_multiply": rw, "alu_op": ra,
+                                                          "fma_op": rates["fma_op"]["per_sm_per_clk"]},
+            "sms": sms, "sm_mhz": sm_max,
+            "sites_per_ns": bound, "frac": sites_per_ns / bound}
+        out["wide_multiply_bound"] = {
+            "basis": f"{ops['wide']:.0f} wide multiplies per site (Philox4x32-10, 20 per 4 sites) "
+                     f"at the measured {rw:.2f} per SM per clock (FMA-heavy pipe)",
+            "sites_per_ns": wide_bound, "frac": sites_per_ns / wide_bound,
+            "folded": {"wide_per_site": WIDE_MUL_PER_SITE_FOLDED, "sites_per_ns": folded,
+                       "frac": sites_per_ns / folded}}
+    return out
+
+
+def single_lattice(args, w, rank, world, stream, rates, sms, with_corr):
+    """One lattice of the workload: device-timed steps, the step recording
+    every sweep, the end-to-end leg through the C ABI, and the roofline of
+    the dominant half-sweep."""
     import torch
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_2503_14688_b300 as P
 
     from paper_2503_14688_b300 import replicas
 
-    stream = torch.cuda.Stream()
     seed = replicas.replica_seed(w.seed, rank)  # replicas: independent lattices, one per rank
     lat = P.Lattice(w.L, w.model, seed=seed, delta=w.delta, stream=stream,
                     record_capacity=args.steps + args.warmup + 4)
@@ -410,8 +488,10 @@ def run_ours(args, w):
     lat.read_records(with_sums=False)
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
     start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(local)
-    if dist:
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    if world > 1:
+        import torch.distributed as dist
+
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
@@ -421,7 +501,7 @@ def run_ours(args, w):
     stop.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
-    if dist:
+    if world > 1:
         dist.barrier()
     ms = start.elapsed_time(stop)
     half0 = [e[0].elapsed_time(e[1]) for e in evs]
@@ -456,81 +536,105 @@ def run_ours(args, w):
         P.xi2([r.M], r.R[None], r.C[None])
     e2e_s = time.perf_counter() - t0
 
-    # axis correlation function C(r) (Eq. (2)) at 12 distances, one pass each
-    corr_r = [1 << k for k in range(12)]
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    sx, sy = lat.correlation(corr_r)
-    corr_s = time.perf_counter() - t0
-    corr = {"distances": corr_r, "ms": 1e3 * corr_s,
-            "lattice_GB_read_per_s": len(corr_r) * 2 * P.Lattice.nbytes(w.model, w.L) / corr_s / 1e9,
-            "C_r": [float(a + b) / (2.0 * float(w.L) ** 2) for a, b in zip(sx, sy)]}
+    corr = None
+    if with_corr:
+        # axis correlation function C(r) (Eq. (2)) at 12 distances, one pass each
+        corr_r = [1 << k for k in range(12)]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sx, sy = lat.correlation(corr_r)
+        corr_s = time.perf_counter() - t0
+        corr = {"distances": corr_r, "ms": 1e3 * corr_s,
+                "lattice_GB_read_per_s": len(corr_r) * 2 * P.Lattice.nbytes(w.model, w.L) / corr_s / 1e9,
+                "C_r": [float(a + b) / (2.0 * float(w.L) ** 2) for a, b in zip(sx, sy)]}
+    lat.close()
 
     ms, e2e_s = replicas.max_over_ranks([ms, e2e_s], device="cuda")
     sites = float(w.L) * float(w.L)
     value = replicas.weak_scaling_value(world, sites, args.steps, ms)
     weak_each = replicas.weak_scaling_value(world, sites, 1, ms_each)
     e2e_value = replicas.weak_scaling_value(world, sites, e2e_steps, e2e_s * 1e3)
-
     sm_max, peak_src = _peaks()
-    peak = SMS * INT_LANES_PER_SM * sm_max * 1e6 / 1e12  # Tops/s
-    dom = half1 if statistics.mean(half1) >= statistics.mean(half0) else half0
-    dom_ms = statistics.mean(dom)
-    ops = ALG_OPS_PER_SITE[w.model] * sites / 2
-    achieved = ops / (dom_ms * 1e-3) / 1e12
-    wide_bound = SMS * WIDE_MUL_PER_SM_CLK / WIDE_MUL_PER_SITE * sm_max * 1e6 / 1e9
+    m0, m1 = statistics.mean(half0), statistics.mean(half1)
+    which = 1 if m1 >= m0 else 0
+    roof = roofline(w.model, sites, max(m0, m1), which, [m0, m1], sms, sm_max, peak_src, rates)
+    return {
+        "value": value, "ms_per_step": ms / args.steps, "steps": args.steps,
+        "config": {"workload": w.name, "model": "ising" if w.model == 0 else "blume_capel",
+                   "L": w.L, "spins": int(sites), "beta": beta, "delta": w.delta,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2_flush": _l2_note(P.Lattice.nbytes(w.model, w.L)),
+                   "step": "host thresholds + half-sweep colour 0 + half-sweep colour 1; "
+                           "every record_every steps an on-device record of B, M, Q, "
+                           "row and column sums",
+                   "record_every": every},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8,
+                "d2h_bytes_per_step": (32 + 8 * w.L) / every, "steps": e2e_steps},
+        "gpu_launches": 2 * args.steps + args.steps // every,
+        "record_every_sweep": {"ms_per_step": ms_each, "value": weak_each, "unit": UNIT,
+                               "steps": n_each,
+                               "overhead_vs_value": value / weak_each - 1.0},
+        "clocks": clk, "xi2_last": xi, "correlation": corr,
+    }
+
+
+def run_ours(args, w):
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    rates = None
+    if not args.no_calib:
+        from paper_2503_14688_b300 import calibrate
+
+        rates = calibrate.measure_rates()
+    stream = torch.cuda.Stream()
+    main = single_lattice(args, w, rank, world, stream, rates, sms, with_corr=True)
     if rank == 0:
         line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": main["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic (hot-start lattice from the seeded Philox)",
-            "config": {"workload": w.name, "model": "ising" if w.model == 0 else "blume_capel",
-                       "L": w.L, "spins": int(sites), "beta": beta, "delta": w.delta,
-                       "parallelism": "replicas" if world > 1 else "single",
-                       "l2_flush": _l2_note(P.Lattice.nbytes(w.model, w.L)),
-                       "step": "host thresholds + half-sweep colour 0 + half-sweep colour 1; "
-                               "every record_every steps an on-device record of B, M, Q, "
-                               "row and column sums",
-                       "record_every": every},
-            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                         "frac": achieved / peak,
-                         "traffic": DRAM_BYTES_PER_SITE[w.model] * sites / 2,
-                         "traffic_basis": "ncu dram__bytes_read.sum + dram__bytes_write.sum of "
-                                          "one half-sweep at L=2^16 (Ising) / 2^15 (Blume-Capel), "
-                                          "scaled by sites per launch; algorithmic "
-                                          f"{0.375 if w.model == wl.ISING else 0.75} B/site",
-                         "kernel": "half-sweep colour %d" % (1 if dom is half1 else 0),
-                         "ops_per_site": ALG_OPS_PER_SITE[w.model],
-                         "peak_basis": f"{SMS} SMs x {INT_LANES_PER_SM} int lanes x "
-                                       f"{sm_max:.0f} MHz ({peak_src})",
-                         "half_sweep_ms": [statistics.mean(half0), statistics.mean(half1)],
-                         "wide_multiply_bound": {
-                             "basis": f"{WIDE_MUL_PER_SITE} wide multiplies per site at "
-                                      f"{WIDE_MUL_PER_SM_CLK} per SM per clock (FMA-heavy pipe)",
-                             "sites_per_ns": wide_bound,
-                             "achieved_sites_per_ns": sites / 2 / (dom_ms * 1e6),
-                             "frac": sites / 2 / (dom_ms * 1e6) / wide_bound}},
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8,
-                    "d2h_bytes_per_step": (32 + 8 * w.L) / every, "steps": e2e_steps},
-            "gpu_launches": 2 * args.steps + args.steps // every,
-            "record_every_sweep": {"ms_per_step": ms_each,
-                                   "value": weak_each, "unit": UNIT, "steps": n_each},
-            "clocks": clk,
-            "xi2_last": xi,
-            "correlation": corr,
+            "config": main["config"], "roofline": main["roofline"], "e2e": main["e2e"],
+            "gpu_launches": main["gpu_launches"],
+            "record_every_sweep": main["record_every_sweep"], "clocks": main["clocks"],
+            "xi2_last": main["xi2_last"], "correlation": main["correlation"],
+            "calibration": rates,
         }
+    # the other single-lattice workload of the large quench: Blume-Capel
+    # Delta = 0 at L = 2^19 (its own roofline, e2e and CPU baseline)
+    if not args.no_bc and w.name.startswith("ising_L1048576"):
+        wb = wl.blume_capel_large()
+        bc = single_lattice(args, wb, rank, world, stream, rates, sms, with_corr=False)
+        if rank == 0:
+            bc.pop("correlation")
+            line["gpu_launches"] += bc["gpu_launches"]
+            if not args.no_cpu_baseline:
+                bc["cpu_baseline"] = cpu_baseline(wb.model, wb.beta, wb.delta)
+            line["blume_capel_large"] = bc
+    if rank == 0:
         if not args.no_batched and world == 1:
             line["batched"] = batched_bench(sweeps=args.batched_sweeps, n_rep=args.batched_replicas)
-            line["served"] = served_bench(n_req=args.served_requests)
+        if not args.no_served and world == 1:
+            line["served"] = served_bench(n_req=args.served_requests,
+                                          n_saturated=args.served_saturated)
         if not args.no_precool and world == 1:
             line["precool"] = precool_bench()
         if not args.no_sw and world == 1:
             line["swendsen_wang"] = sw_bench()
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(w.model, beta, w.delta)
+            line["cpu_baseline"] = cpu_baseline(w.model, w.beta, w.delta)
         print(json.dumps(line), flush=True)
-    lat.close()
     if dist:
         dist.destroy_process_group()
 
@@ -552,7 +656,15 @@ def main():
     ap.add_argument("--L", type=int, default=0, help="override the workload's L (profiling)")
     ap.add_argument("--batched-replicas", type=int, default=4096)
     ap.add_argument("--batched-sweeps", type=int, default=10000)
-    ap.add_argument("--served-requests", type=int, default=48)
+    ap.add_argument("--served-requests", type=int, default=2000,
+                    help="requests of the served stream's Poisson leg")
+    ap.add_argument("--served-saturated", type=int, default=200,
+                    help="requests (the stream's first) of the saturated capacity leg")
+    ap.add_argument("--no-served", action="store_true", help="skip the served stream")
+    ap.add_argument("--no-bc", action="store_true",
+                    help="skip the Blume-Capel L=2^19 single-lattice sub-object")
+    ap.add_argument("--no-calib", action="store_true",
+                    help="skip the run-time integer-rate calibration (no pipe-aware bound)")
     ap.add_argument("--only-batched", action="store_true",
                     help="print only the replica-ensemble measurement (profiling)")
     args = ap.parse_args()

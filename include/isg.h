@@ -215,12 +215,14 @@ isg_status isg_measure(isg_lattice *lat, isg_obs *out);
  * image, which every GPU that loads the library holds until the process
  * exits.  L above that limit is rejected with ISG_ERR_INVALID (use
  * isg_measure).  The first call on each device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Each call clears the part of the array it
+ * address (cudaGetSymbolAddress) with that device current and keeps it for
+ * the life of the process; make that first call before any stream capture,
+ * and do not reset the device (cudaDeviceReset) while the library is
+ * loaded, since the kept address would then be stale.  Each call clears the part of the array it
  * uses before accumulating.  All calls on one device share the array: calls
  * whose GPU work overlaps (for instance from two host threads on two
  * streams) race on it and their results are undefined; calls made one after
- * another never overlap, since each waits for its stream. */
+ * another never overlap, since each waits for its stream, on failure too. */
 isg_status isg_measure_planes_noalloc(int32_t model, int64_t L, const void *d_planes,
                                       void *stream, int64_t sweep, isg_obs *out);
 

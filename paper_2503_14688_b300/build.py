@@ -34,11 +34,10 @@ def _sources():
 
 
 def _stale():
-    for lib in (LIB, CALIB_LIB):
-        if not os.path.exists(lib):
-            return True
-    t = min(os.path.getmtime(LIB), os.path.getmtime(CALIB_LIB))
-    return any(os.path.getmtime(s) > t for s in _sources() + [os.path.join(CSRC, "isg_calib.cu")])
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(s) > t for s in _sources())
 
 
 def build(force: bool = False, verbose: bool = False) -> str:
@@ -64,12 +63,22 @@ def build(force: bool = False, verbose: bool = False) -> str:
     tmp = LIB + ".tmp.%d" % os.getpid()
     subprocess.run([NVCC, "-shared", *ARCH, "-o", tmp, *objs], check=True)
     os.replace(tmp, LIB)
-    # integer-throughput calibration kernels (roofline measurement tool)
+    return LIB
+
+
+def build_calib(force: bool = False) -> str:
+    """Build the integer-throughput calibration kernels (libisg_calib.so), a
+    measurement tool of the benchmark's roofline; not part of libisg."""
+    src = os.path.join(CSRC, "isg_calib.cu")
+    deps = [src] + [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
+    if (not force and os.path.exists(CALIB_LIB)
+            and all(os.path.getmtime(d) <= os.path.getmtime(CALIB_LIB) for d in deps)):
+        return CALIB_LIB
     tmp = CALIB_LIB + ".tmp.%d" % os.getpid()
     subprocess.run([NVCC, "-shared", "-O3", "-std=c++17", *ARCH, "-lineinfo", "-Xcompiler", "-fPIC",
-                    os.path.join(CSRC, "isg_calib.cu"), "-o", tmp], check=True)
+                    "-I", INCLUDE, "-I", CSRC, src, "-o", tmp], check=True)
     os.replace(tmp, CALIB_LIB)
-    return LIB
+    return CALIB_LIB
 
 
 def clean():

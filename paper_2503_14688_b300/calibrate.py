@@ -34,15 +34,56 @@ def sm_clock_mhz():
         return None
 
 
+def _load():
+    from paper_2503_14688_b300 import build
+
+    build.build_calib()
+    lib = ctypes.CDLL(LIB)
+    lib.isg_calib_run.restype = ctypes.c_float
+    lib.isg_calib_run.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p]
+    return lib
+
+
+# The three rates the sweep's pipe-aware bound needs, as operations per SM
+# per clock: the 32x32 -> 64 (high-half) multiply of Philox on the FMA-heavy
+# pipe, a single-cycle logic op on the ALU pipe, a low-half multiply-add on
+# the FMA-heavy pipe.
+PIPE_KINDS = {"wide_multiply": 1, "alu_op": 7, "fma_op": 2}
+
+
+def measure_rates(kinds=PIPE_KINDS, iters=20000):
+    """Operations per SM per clock of each kind, on the current device.  The
+    SM count comes from the device; the clock is the highest of two
+    nvidia-smi samples taken around each timed launch (each about 0.25 s)."""
+    import torch
+
+    lib = _load()
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    blocks, threads = sms * 8, 256
+    sink = torch.zeros(blocks, dtype=torch.int32, device="cuda")
+    out = {"sms": sms}
+    for name, kind in kinds.items():
+        if lib.isg_calib_run(kind, blocks, threads, 100, sink.data_ptr()) < 0:  # warm-up
+            raise RuntimeError("calibration kernel %d failed" % kind)
+        mhz0 = sm_clock_mhz()
+        ms = lib.isg_calib_run(kind, blocks, threads, iters, sink.data_ptr())
+        mhz1 = sm_clock_mhz()
+        if ms <= 0:
+            raise RuntimeError("calibration kernel %d failed" % kind)
+        mhz = max([m for m in (mhz0, mhz1) if m is not None] or [2032.0])
+        ops = blocks * threads * iters * KINDS[kind][1]
+        out[name] = {"per_sm_per_clk": ops / (ms * 1e-3) / sms / (mhz * 1e6), "sm_mhz": mhz,
+                     "ms": ms}
+    return out
+
+
 def main():
     import torch
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--json", default=None)
     args = ap.parse_args()
-    lib = ctypes.CDLL(LIB)
-    lib.isg_calib_run.restype = ctypes.c_float
-    lib.isg_calib_run.argtypes = [ctypes.c_int] * 4 + [ctypes.c_void_p]
+    lib = _load()
     props = torch.cuda.get_device_properties(0)
     sms = props.multi_processor_count
     blocks, threads = sms * 8, 256

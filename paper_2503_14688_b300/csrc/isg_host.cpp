@@ -181,9 +181,8 @@ double xi2_fp64(int64_t n, int64_t L, const int64_t *M, const int32_t *R, const 
     return std::sqrt(s0avg / skavg - 1.0) / (2.0 * std::sin(M_PI / (double)L));
 }
 
-// Integral coherence length (Appendix C): xi = I2 / I1 with
-// I_n = int_0^{r_cut} r^n C(r) dr, by the trapezoid rule over the sampled
-// distances r[0] < r[1] < ... (those beyond r_cut are ignored).
+// Swendsen-Wang bond threshold (Appendix B): rne(2^32 p), p the probability
+// that a bond between aligned +-1 neighbours is active.
 uint64_t sw_threshold(double beta)
 {
     // p = 1 - e^{-2 beta} (J = 1: aligned +-1 neighbours lie 2 below
@@ -191,6 +190,9 @@ uint64_t sw_threshold(double beta)
     return (uint64_t)std::llrint(std::ldexp(-std::expm1(-2.0 * beta), 32));
 }
 
+// Integral coherence length (Appendix C): xi = I2 / I1 with
+// I_n = int_0^{r_cut} r^n C(r) dr, by the trapezoid rule over the sampled
+// distances r[0] < r[1] < ... (those beyond r_cut are ignored).
 double xi_integral_fp64(int64_t n, const double *r, const double *c, double r_cut)
 {
     if (n < 2 || !r || !c)

@@ -34,7 +34,9 @@ void *g_scratch_addr[kMaxDevices] = {};  // device address of the array, per dev
 
 // The device address of isg_noalloc_scratch on the current device.  The
 // symbol's name is only a host-side stand-in, so its address is looked up
-// once per device (with that device current) and remembered.
+// once per device (with that device current) and remembered for the life
+// of the process; a device reset (cudaDeviceReset, or the primary context
+// torn down and created again) would leave the remembered address stale.
 isg_status scratch_address(void **out)
 {
     int dev = -1;
@@ -97,6 +99,7 @@ extern "C" isg_status isg_measure_planes_noalloc(int32_t model, int64_t L, const
 
     // The array keeps the previous call's sums: clear this call's record first.
     cudaError_t e = cudaMemsetAsync(scratch, 0, bytes, s);
+    const bool queued = e == cudaSuccess;  // from here on, work on the array may be in flight
     if (e == cudaSuccess)
         e = isg::launch_measure(pl, scratch, sweep, s);
     int64_t hdr[4] = {0, 0, 0, 0};
@@ -113,6 +116,12 @@ extern "C" isg_status isg_measure_planes_noalloc(int32_t model, int64_t L, const
         e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaGetLastError();
+        // No call returns while its work on the shared array may still run:
+        // a following call on another stream would otherwise race with it.
+        if (queued) {
+            cudaStreamSynchronize(s);
+            cudaGetLastError();
+        }
         return isg::report_error(ISG_ERR_CUDA, "isg_measure_planes_noalloc: %s",
                                  cudaGetErrorString(e));
     }
