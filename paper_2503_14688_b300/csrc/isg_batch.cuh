@@ -94,8 +94,7 @@ struct Team {
 size_t smem_bytes_for(int32_t model, int64_t L)
 {
     const size_t planes = (size_t)L * (size_t)L / (model == ISG_ISING ? 8 : 4);
-    const size_t spread = model == ISG_ISING ? 0 : sizeof(uint32_t) * kBcSpread * kBcNibbleTable;
-    return planes + 8 * (size_t)L + 4 * kBcTableSize + 64 + spread;
+    return planes + 8 * (size_t)L + 4 * kBcTableSize + 64;
 }
 
 // ---------------------------------------------------------------------------
@@ -237,8 +236,7 @@ __device__ void smem_measure(const Team<kHalf> &team, const uint32_t *P, int L, 
 template <bool kFull>
 __device__ __forceinline__ void bc_smem_colour(uint32_t *P, int L, int W, int c, int y, int w,
                                                int dy, int dw, uint64_t qrow,
-                                               const PhiloxLaunch &pc, const uint32_t *s_thr,
-                                               const uint32_t *s_nib)
+                                               const PhiloxLaunch &pc, const uint32_t *s_thr)
 {
     const int LW = L * W;
     const uint32_t *nbn = P + 2 * (1 - c) * LW, *nbp = nbn + LW;
@@ -254,7 +252,7 @@ __device__ __forceinline__ void bc_smem_colour(uint32_t *P, int L, int W, int c,
                                 side_word(sp, nbp[y * W + ew], par)};
         uint32_t n = tn[y * W + w], p = tp[y * W + w];
         const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)w;
-        bc_word_update<kFull>(n, p, nn, pp, q0, pc, s_thr, s_nib);
+        bc_word_update<kFull>(n, p, nn, pp, q0, pc, s_thr);
         tn[y * W + w] = n;
         tp[y * W + w] = p;
         w += dw;
@@ -277,14 +275,11 @@ __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem,
     int32_t *C_s = R_s + L;
     uint32_t *s_thr = reinterpret_cast<uint32_t *>(C_s + L);
     unsigned long long *acc = reinterpret_cast<unsigned long long *>(s_thr + kBcTableSize);
-    uint32_t *s_nib = reinterpret_cast<uint32_t *>(acc + 4);  // Blume-Capel only
 
     const uint4 *g4 = reinterpret_cast<const uint4 *>(it.planes);
     uint4 *s4 = reinterpret_cast<uint4 *>(P);
     for (int i = tid; i < nplanes * LW / 4; i += nt)
         s4[i] = g4[i];
-    if (MODEL == 1)
-        bc_spread_fill(s_nib, tid, nt);
     team.sync();
 
     const int dy = nt / W, dw = nt - (nt / W) * W;
@@ -331,9 +326,9 @@ __device__ void run_replica(const EnsItem &it, const EnsArgs &a, uint32_t *smem,
                     }
                 }
             } else if (bc_full) {
-                bc_smem_colour<true>(P, L, W, c, y, w, dy, dw, qrow, pc, s_thr, s_nib);
+                bc_smem_colour<true>(P, L, W, c, y, w, dy, dw, qrow, pc, s_thr);
             } else {
-                bc_smem_colour<false>(P, L, W, c, y, w, dy, dw, qrow, pc, s_thr, s_nib);
+                bc_smem_colour<false>(P, L, W, c, y, w, dy, dw, qrow, pc, s_thr);
             }
             team.sync();
         }

@@ -35,22 +35,26 @@ struct IsingThr {
     uint32_t full4, full8;
 };
 
-// Blume-Capel acceptance table: entry g + 9 (n + p) + 64 b for the current
-// value s (n = s != 0, p = s > 0, so n + p is 0, 1, 2 for s = 0, -1, +1),
-// the proposal bit b and g = h + 4 in [0, 8] (h = neighbour sum).  The rule
-// is v < thr31 with v = u >> 1 and thr31 = rne(2^31 p) (2^31 = always).
+// Blume-Capel acceptance table: entry (g & 7) | p << 3 | n << 4 | (g >> 3) << 5
+// | b << 6 for the current value s (n = s != 0, p = s > 0), the proposal bit
+// b and g = h + 4 in [0, 8] (h = neighbour sum): the bits the half-sweep
+// gathers per site from its bit-planes.  The rule is v < thr31 with
+// v = u >> 1 and thr31 = rne(2^31 p) (2^31 = always).
 //   full = 1 (every thr31 >= 1): entry = 2 thr31 - 1 (mod 2^32), and the
 //            site accepts iff u <= entry -- the same decision, since
 //            u = 2 v + b;
 //   full = 0 (some move can never be accepted): entry = thr31, accept iff
 //            (u >> 1) < entry.
-// Entries 27..63 and 91..127 are unused.
+// Entries of no state (p without n, g > 8) are unused.
 constexpr int kBcTableSize = 128;
 struct BcTable {
     uint32_t thr[kBcTableSize];
     uint32_t full;
 };
-__host__ __device__ constexpr int bc_entry(int n, int p, int b, int g) { return g + 9 * (n + p) + 64 * b; }
+__host__ __device__ constexpr int bc_entry(int n, int p, int b, int g)
+{
+    return (g & 7) | (p << 3) | (n << 4) | ((g >> 3) << 5) | (b << 6);
+}
 
 // Device-side description of one lattice's spin planes.
 //   Ising:        plane(c)    = base + c * L * W          (bit = s > 0)

@@ -260,9 +260,10 @@ __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
 // ---------------------------------------------------------------------------
 // Blume-Capel half-sweep.  Two bit-planes per colour: n (s != 0) and p (s > 0).
 // The neighbour field h + 4 = #(+1 neighbours) + #(neighbours != -1) is a
-// bit-sliced sum of eight indicator words (four bits g0..g3); each site
-// then looks its threshold up in the table of BcTable, indexed by
-// (proposal bit, n + p, h + 4) and held in shared memory.
+// bit-sliced sum of eight indicator words (four bits g0..g3); the six
+// planes g0..g3, p, n are transposed into one index byte per site, and each
+// site looks its threshold up in the table of BcTable, indexed by that byte
+// and its proposal bit, held in shared memory.
 // ---------------------------------------------------------------------------
 template <int V, bool kFull>
 __device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ tn_plane,
@@ -270,7 +271,7 @@ __device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ t
                                              const uint32_t *__restrict__ nn_plane,
                                              const uint32_t *__restrict__ np_plane, int64_t L,
                                              int64_t W, int colour, int H, const PhiloxLaunch &pc,
-                                             const uint32_t *s_thr, const uint32_t *s_nib)
+                                             const uint32_t *s_thr)
 {
     // rows and words fit 32 bits; row pointers advance by one row per step
     const uint32_t Li = (uint32_t)L, Wi = (uint32_t)W;
@@ -308,7 +309,7 @@ __device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ t
             const uint32_t nbn[4] = {Un.v[v], Dn.v[v], Sn.v[v], Xn.v[v]};
             const uint32_t nbp[4] = {Up.v[v], Dp.v[v], Sp.v[v], Xp.v[v]};
             const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)(w0 + v);
-            bc_word_update<kFull>(Tn.v[v], Tp.v[v], nbn, nbp, q0, pc, s_thr, s_nib);
+            bc_word_update<kFull>(Tn.v[v], Tp.v[v], nbn, nbp, q0, pc, s_thr);
         }
         store_words<V>(trow + w0, Tn);
         store_words<V>(trow + dtp + w0, Tp);
@@ -328,13 +329,11 @@ __global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
               int64_t L, int64_t W, int colour, int H, PhiloxLaunch pc, BcTable tab)
 {
     __shared__ uint32_t s_thr[kBcTableSize];
-    __shared__ uint32_t s_nib[kBcSpread * kBcNibbleTable];
     for (int i = threadIdx.x; i < kBcTableSize; i += blockDim.x)
         s_thr[i] = tab.thr[i];
-    bc_spread_fill(s_nib, threadIdx.x, blockDim.x);
     __syncthreads();
     bc_half_band<V, kFull>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, tn_plane, tp_plane,
-                           nn_plane, np_plane, L, W, colour, H, pc, s_thr, s_nib);
+                           nn_plane, np_plane, L, W, colour, H, pc, s_thr);
 }
 
 // Blume-Capel lattices of one side L in one launch (see k_ising_half_multi).
@@ -343,17 +342,15 @@ __global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
     k_bc_half_multi(int64_t L, int colour, int H, BcTable tab, const __grid_constant__ MultiArgs a)
 {
     __shared__ uint32_t s_thr[kBcTableSize];
-    __shared__ uint32_t s_nib[kBcSpread * kBcNibbleTable];
     for (int i = threadIdx.x; i < kBcTableSize; i += blockDim.x)
         s_thr[i] = tab.thr[i];
-    bc_spread_fill(s_nib, threadIdx.x, blockDim.x);
     __syncthreads();
     const int r = blockIdx.y;
     const int64_t W = L / 64, LW = L * W;
     uint32_t *tn = a.planes[r] + (int64_t)(2 * colour) * LW;
     const uint32_t *nn = a.planes[r] + (int64_t)(2 * (1 - colour)) * LW;
     bc_half_band<V, kFull>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, tn, tn + LW, nn, nn + LW,
-                           L, W, colour, H, a.pc[r], s_thr, s_nib);
+                           L, W, colour, H, a.pc[r], s_thr);
 }
 
 // ---------------------------------------------------------------------------

@@ -96,33 +96,89 @@ __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uin
     cy = (a & b) | (c & (a ^ b));
 }
 
-// Blume-Capel per-site threshold lookup.  A site's table entry is
-// g + 9 (n + p) + 64 b (BcTable); as a byte offset into the u32 table,
-// 4 (g + 9 (n + p)) + 256 b.
+// Blume-Capel per-site threshold lookup.  A site's table entry (BcTable,
+// bc_entry) has the bits (g0, g1, g2, p, n, g3, b): the field g = h + 4 in
+// four bits, the spin planes p, n and the proposal bit b = u & 1.  As a byte
+// offset into the u32 table that is 4 * (low six bits) + 256 b.
 //
-// The six planes g0..g3, p, n are known before the random numbers.  Their
-// bits are turned into one byte per site, 4 (g + 9 (n + p)) <= 104, four
-// sites at a time: each plane's nibble of the four sites indexes a 16-entry
-// table (kBcSpread tables in shared memory, one per plane) whose entry holds
-// the plane's weight (4, 8, 16, 32 for g0..g3, 36 for p and n) in the byte of
-// every site whose bit is set; the six entries are added.  Sixteen-entry
-// tables span half the shared-memory banks, so the 32 lanes of a warp never
-// conflict on them.  Per site, one byte permute then joins the index byte
-// with the proposal bit b = u & 1 at bit 8.
-constexpr int kBcSpread = 6;
-constexpr int kBcNibbleTable = 16;
+// The six planes g0..g2, p, n, g3 are known before the random numbers.
+// Their bits become one byte per site -- plane bits at byte bits 2..7, so
+// the byte is already the entry's offset -- by transposing the bit matrix
+// (8 plane words x 32 sites) into 8 words of 4 site bytes: five exchange
+// stages, each swapping one bit of the word index with one bit of the bit
+// position between pairs of words.  Word i of the result then holds sites
+// 4i .. 4i+3 (one Philox call), byte k being site 4i + k.  Per site one byte
+// permute joins the index byte with b at bit 8.
 
-__device__ __forceinline__ void bc_spread_fill(uint32_t *s_nib, int tid, int nt)
+// Exchange between words a (index bit 0) and c (index bit 1) of the
+// position bit of value d (mask m: positions where that bit is 0): a's bits
+// at the positions outside m trade places with c's bits d lower.  (A
+// select-by-mask form with one op fewer per pair measured 1% slower.)
+__device__ __forceinline__ void bit_exchange(uint32_t &a, uint32_t &c, int d, uint32_t m)
 {
-    for (int i = tid; i < kBcSpread * kBcNibbleTable; i += nt) {
-        const int k = i / kBcNibbleTable, v = i % kBcNibbleTable;
-        const uint32_t weight = k < 4 ? 4u << k : 36u;
-        uint32_t e = 0;
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-            e += (uint32_t)((v >> m) & 1) * (weight << (8 * m));
-        s_nib[i] = e;
-    }
+    const uint32_t t = ((a >> d) ^ c) & m;
+    c ^= t;
+    a ^= t << d;
+}
+
+// The same for position bit 4 (halves) and 3 (bytes), by byte permutes.
+__device__ __forceinline__ void half_exchange(uint32_t &a, uint32_t &c)
+{
+    const uint32_t lo = __byte_perm(a, c, 0x5410u);
+    c = __byte_perm(a, c, 0x7632u);
+    a = lo;
+}
+
+__device__ __forceinline__ void byte_exchange(uint32_t &a, uint32_t &c)
+{
+    const uint32_t ev = __byte_perm(a, c, 0x6240u);
+    c = __byte_perm(a, c, 0x7351u);
+    a = ev;
+}
+
+// Index bytes of the 32 sites: out[i] byte k = site 4i + k, bits 2..7 =
+// (g0, g1, g2, p, n, g3).  Word index bits start as the byte bit each plane
+// is headed for (in the order the stages leave them: plane word j ends at
+// byte bit 4 (j & 1) + 2 ((j >> 2) & 1) + ((j >> 1) & 1), so words 0 and 2,
+// headed for bits 0 and 1, are zero).
+__device__ __forceinline__ void bc_index_bytes(uint32_t g0, uint32_t g1, uint32_t g2, uint32_t g3,
+                                               uint32_t p, uint32_t n, uint32_t (&o)[8])
+{
+    o[0] = 0u;
+    o[1] = g2;
+    o[2] = 0u;
+    o[3] = p;
+    o[4] = g0;
+    o[5] = n;
+    o[6] = g1;
+    o[7] = g3;
+    // word bit 2 <-> position bit 1 (words 0 and 2 are zero)
+    o[0] = (o[4] << 2) & 0xCCCCCCCCu;
+    o[4] &= 0xCCCCCCCCu;
+    o[2] = (o[6] << 2) & 0xCCCCCCCCu;
+    o[6] &= 0xCCCCCCCCu;
+    bit_exchange(o[1], o[5], 2, 0x33333333u);
+    bit_exchange(o[3], o[7], 2, 0x33333333u);
+    // word bit 1 <-> position bit 0
+    bit_exchange(o[0], o[2], 1, 0x55555555u);
+    bit_exchange(o[1], o[3], 1, 0x55555555u);
+    bit_exchange(o[4], o[6], 1, 0x55555555u);
+    bit_exchange(o[5], o[7], 1, 0x55555555u);
+    // word bit 2 <-> position bit 4
+    half_exchange(o[0], o[4]);
+    half_exchange(o[1], o[5]);
+    half_exchange(o[2], o[6]);
+    half_exchange(o[3], o[7]);
+    // word bit 1 <-> position bit 3
+    byte_exchange(o[0], o[2]);
+    byte_exchange(o[1], o[3]);
+    byte_exchange(o[4], o[6]);
+    byte_exchange(o[5], o[7]);
+    // word bit 0 <-> position bit 2
+    bit_exchange(o[0], o[1], 4, 0x0F0F0F0Fu);
+    bit_exchange(o[2], o[3], 4, 0x0F0F0F0Fu);
+    bit_exchange(o[4], o[5], 4, 0x0F0F0F0Fu);
+    bit_exchange(o[6], o[7], 4, 0x0F0F0F0Fu);
 }
 
 // Blume-Capel: new (n, p) target words.  Neighbour planes nbn/nbp hold the
@@ -133,8 +189,7 @@ __device__ __forceinline__ void bc_spread_fill(uint32_t *s_nib, int tid, int nt)
 template <bool kFull>
 __device__ __forceinline__ void bc_word_update(uint32_t &n, uint32_t &p, const uint32_t (&nbn)[4],
                                                const uint32_t (&nbp)[4], uint64_t q0,
-                                               const PhiloxLaunch &pc, const uint32_t *s_thr,
-                                               const uint32_t *s_nib)
+                                               const PhiloxLaunch &pc, const uint32_t *s_thr)
 {
     // eight indicators: s_i = +1 (n & p), s_i != -1 (~n | p)
     const uint32_t x0 = nbn[0] & nbp[0], x1 = ~nbn[0] | nbp[0];
@@ -150,38 +205,22 @@ __device__ __forceinline__ void bc_word_update(uint32_t &n, uint32_t &p, const u
     const uint32_t g1 = se ^ cd, cf = se & cd;
     const uint32_t g2 = ce ^ cf;  // weight-4 column
     const uint32_t g3 = ce & cf;  // only when h + 4 = 8
-    const uint32_t planes[kBcSpread] = {g0, g1, g2, g3, p, n};
-    // byte m of ev[k] (od[k]): nibble 2m (2m + 1) of plane k, times 4 -- the
-    // byte offset of its entry in table k
-    uint32_t ev[kBcSpread], od[kBcSpread];
-#pragma unroll
-    for (int k = 0; k < kBcSpread; ++k) {
-        ev[k] = (planes[k] << 2) & 0x3C3C3C3Cu;
-        od[k] = (planes[k] >> 2) & 0x3C3C3C3Cu;
-    }
+    uint32_t idx[8];
+    bc_index_bytes(g0, g1, g2, g3, p, n, idx);
 
     const char *thr_bytes = reinterpret_cast<const char *>(s_thr);
-    const char *nib_bytes = reinterpret_cast<const char *>(s_nib);
     const PhiloxWordPart wp = philox_word_part(pc, (uint32_t)(q0 >> 32));
     // one chain over the 32 sites, site 31 first: acc ends with site b at
     // bit b; bits (a right funnel shift) with site b at bit 31 - b
     uint32_t acc = 0, bits = 0;
 #pragma unroll
     for (int i = 7; i >= 0; --i) {
-        // 4 (g + 9 (n + p)) of sites 4i .. 4i+3, one byte each
-        const uint32_t *src = (i & 1) ? od : ev;
-        uint32_t word = 0;
-#pragma unroll
-        for (int k = 0; k < kBcSpread; ++k) {
-            const uint32_t off = __byte_perm(src[k], 0u, 0x4440u | (uint32_t)(i >> 1));
-            word += *reinterpret_cast<const uint32_t *>(nib_bytes + k * 4 * kBcNibbleTable + off);
-        }
         uint32_t r[4];
         philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
 #pragma unroll
         for (int kk = 3; kk >= 0; --kk) {
-            // byte kk of word (the site's index) and bit 0 of u (b) at bit 8
-            const uint32_t off = __byte_perm(word, r[kk], 0x0040u | (uint32_t)kk) & 0x1FCu;
+            // byte kk of idx[i] (the site's entry offset) and bit 0 of u (b) at bit 8
+            const uint32_t off = __byte_perm(idx[i], r[kk], 0x0040u | (uint32_t)kk) & 0x1FCu;
             const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
             if (kFull)
                 acc = shift_in_not_below(acc, thr, r[kk]);       // + (entry >= u): accept
