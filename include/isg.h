@@ -374,6 +374,87 @@ double isg_server_clock(const isg_server *srv);
 isg_status isg_server_stats(const isg_server *srv, double *flips_done, size_t *bytes_in_use,
                             size_t *budget);
 
+/* ---------------------------------------------------------------------------
+ * Row slabs: the domain decomposition with which the paper runs ONE lattice
+ * on many GPUs (Introduction; Table I: L = 2^22 on 64 GPUs).  A slab owns
+ * the global rows y0 .. y0 + rows - 1 of an L x L lattice (one slab per
+ * process or GPU) and keeps, per colour, one halo row above (global row
+ * y0 - 1, periodic) and one below (global row y0 + rows).
+ *
+ * One sweep t of the whole lattice, on every slab:
+ *   1. colour-1 halos: isg_slab_edges(colour 1) -> first / last owned row;
+ *      each slab's first row goes to the slab above as its `below` halo and
+ *      its last row to the slab below as its `above` halo (periodic, a
+ *      single slab is its own neighbour); isg_slab_set_halos(colour 1);
+ *   2. isg_slab_half_sweep(colour 0, beta(t));
+ *   3. the same exchange for colour 0;
+ *   4. isg_slab_half_sweep(colour 1, beta(t)).
+ * Random words are keyed by the global site, so the slabs together evolve
+ * bit for bit as the lattice created whole with the same seed.  After a
+ * sweep the colour-0 halos are current (the colour-1 halos are one
+ * half-sweep old), and isg_slab_measure gives the slab's part of every
+ * observable: the lattice's B, M and Q are the sums over slabs, its row
+ * sums the slabs' row sums in slab order, its column sums the sums of the
+ * slabs' column sums.  No call moves data between
+ * slabs: the caller does (host memory, peer copies or a collective
+ * library), so the library itself stays single-GPU.
+ * ------------------------------------------------------------------------- */
+typedef struct isg_slab isg_slab;
+
+typedef struct {
+    int32_t model;    /* ISG_ISING or ISG_BLUME_CAPEL                           */
+    int64_t L;        /* side of the whole lattice (a valid L)                  */
+    int64_t y0;       /* first owned global row: a multiple of 16               */
+    int64_t rows;     /* owned rows: a multiple of 16, >= 16, y0 + rows <= L    */
+    uint64_t seed;    /* Philox key of the whole lattice                        */
+    double delta;     /* Blume-Capel crystal field                              */
+    void *stream;     /* cudaStream_t for all work, NULL = default stream       */
+} isg_slab_desc;
+
+/* Bytes of one edge or halo row of one colour: L/16 (Ising) or L/8
+ * (Blume-Capel: the occupancy words, then the sign words), in the plane
+ * layout of isg_save.  0 if the model or L is invalid. */
+size_t isg_slab_edge_bytes(int32_t model, int64_t L);
+
+/* Allocate the slab's planes ((rows + 2) rows per colour plane) on the
+ * current device; spins undefined, halos zero.  *out NULL on failure. */
+isg_status isg_slab_create(const isg_slab_desc *desc, isg_slab **out);
+/* Free everything (waits for the stream).  NULL accepted. */
+void isg_slab_destroy(isg_slab *slab);
+/* Hot start of the owned rows, equal to those rows of the whole lattice's
+ * isg_lattice_init_random; sweep counter 0. */
+isg_status isg_slab_init_random(isg_slab *slab);
+/* Owned rows from / to rows*L host bytes s[(y - y0) L + x]; set also sets the
+ * sweep counter to t.  ISG_ERR_INVALID on a value outside the model's set.
+ * Synchronise. */
+isg_status isg_slab_set(isg_slab *slab, const int8_t *host, int64_t t);
+isg_status isg_slab_get(isg_slab *slab, int8_t *out);
+/* Copy colour `colour`'s first and last owned rows (isg_slab_edge_bytes
+ * each) to caller memory, host or device (any pointer the CUDA runtime can
+ * address).  Queued on the stream; waits for it when a destination is host
+ * memory. */
+isg_status isg_slab_edges(isg_slab *slab, int32_t colour, void *first, void *last);
+/* Load colour `colour`'s halo rows: `above` = global row y0 - 1 (the last
+ * row of the slab above), `below` = global row y0 + rows (the first row of
+ * the slab below).  Host or device memory; waits for the stream when a
+ * source is host memory. */
+isg_status isg_slab_set_halos(isg_slab *slab, int32_t colour, const void *above,
+                              const void *below);
+/* Half-sweep of colour `colour` of the owned rows at the slab's sweep
+ * counter t with inverse temperature beta (reads the other colour's halos).
+ * Colour 1 completes the sweep and advances the counter.  Asynchronous. */
+isg_status isg_slab_half_sweep(isg_slab *slab, int32_t colour, double beta);
+/* The slab's observables: B over the four bonds of every owned colour-1
+ * site (every bond joins a colour-0 and a colour-1 site, so the slabs' B
+ * add up to the lattice's; reads the colour-0 halos, current after a
+ * sweep), M, Q, row_sums[0..rows) of the owned rows and col_sums[0..L) of
+ * the owned part of each column, into caller HOST arrays (either may be
+ * NULL); out->sweep = the sweep counter.  Synchronises. */
+isg_status isg_slab_measure(isg_slab *slab, isg_obs *out);
+/* Sweep counter, L, y0, rows, model. */
+isg_status isg_slab_info(const isg_slab *slab, int64_t *sweep, int64_t *L, int64_t *y0,
+                         int64_t *rows, int32_t *model);
+
 /* Correlation function along the axes (Eq. (2)) of the current lattice: for
  * each distance r[k] (0 <= r[k] < L) the exact sums
  *   out_x[k] = sum_{x,y} s(x,y) s(x + r[k], y),

@@ -21,6 +21,9 @@ Parity status of each function (what pins it is in ``tests/test_oracle_*``):
                   constructed lattices (tests/test_oracle_correlation.py)
   window_init/run pinned: equal to init_random/run on the interior of the
                   light cone (tests/test_oracle_windows.py)
+  slab_half_sweep pinned: row slabs with halos exchanged every half-sweep
+  slab_measure    reproduce run / measure of the whole lattice
+                  (tests/test_oracle_slab.py)
 """
 import ctypes
 import os
@@ -79,6 +82,12 @@ def lib():
                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
                                         ctypes.c_uint64, ctypes.c_int64, f64p, ctypes.c_double]
         L.oracle_window_run.restype = ctypes.c_int
+        L.oracle_slab_half_sweep.argtypes = [i8p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                             ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64,
+                                             ctypes.c_int, ctypes.c_double, ctypes.c_double]
+        L.oracle_slab_half_sweep.restype = ctypes.c_int
+        L.oracle_slab_measure.argtypes = [i8p, ctypes.c_int64, ctypes.c_int64, i64p, i32p, i32p]
+        L.oracle_slab_measure.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -233,3 +242,29 @@ def swendsen_wang(s: np.ndarray, seed: int, k: int, beta: float):
     if n < 0:
         raise ValueError("oracle_swendsen_wang rejected its arguments")
     return labels, int(n)
+
+
+def slab_half_sweep(s: np.ndarray, y0: int, model: int, seed: int, t: int, c: int, beta: float,
+                    delta: float = 0.0):
+    """Half-sweep of colour c of a row slab in place: s is (rows + 2) x L,
+    rows 1..rows the owned global rows y0.., rows 0 and rows + 1 the halos."""
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    rows, L = s.shape[0] - 2, s.shape[1]
+    rc = lib().oracle_slab_half_sweep(_ptr(s, ctypes.c_int8), rows, L, y0, model,
+                                      seed & (2**64 - 1), t, c, float(beta), float(delta))
+    if rc != 0:
+        raise ValueError("oracle_slab_half_sweep rejected its arguments")
+
+
+def slab_measure(s: np.ndarray):
+    """(B, M, Q, R[rows], C[L]) of the owned rows of a slab (see slab_half_sweep)."""
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    rows, L = s.shape[0] - 2, s.shape[1]
+    bmq = np.zeros(3, dtype=np.int64)
+    R = np.zeros(rows, dtype=np.int32)
+    C = np.zeros(L, dtype=np.int32)
+    rc = lib().oracle_slab_measure(_ptr(s, ctypes.c_int8), rows, L, _ptr(bmq, ctypes.c_int64),
+                                   _ptr(R, ctypes.c_int32), _ptr(C, ctypes.c_int32))
+    if rc != 0:
+        raise ValueError("oracle_slab_measure rejected its arguments")
+    return int(bmq[0]), int(bmq[1]), int(bmq[2]), R, C

@@ -495,6 +495,90 @@ int oracle_window_run(int8_t *s, int64_t h, int64_t w, int64_t y0, int64_t x0, i
 }
 
 /* ------------------------------------------------------------------------ */
+/* Row slabs of a lattice (domain decomposition, Introduction: the paper     */
+/* runs one lattice on many GPUs, each holding a part of it).                */
+/* ------------------------------------------------------------------------ */
+
+/* Value of a site after its Metropolis update: current value si, neighbour
+ * sum h, random word u (Eq. (1) with J = 1; the acceptance and proposal
+ * rules stated at the top of this file).                                   */
+static int metropolis_new_value(int si, int h, uint32_t u, int model, double beta, double delta)
+{
+    if (model == ORACLE_ISING) {
+        const double dE = (double)(2 * si * h);
+        if (dE > 0.0 && !((uint64_t)u < threshold_bits(beta, dE, 32)))
+            return si;
+        return -si;
+    }
+    const int s2 = oracle_bc_proposal(si, (int)(u & 1u));
+    const double dE = bc_delta_energy(si, s2, h, delta);
+    if (dE > 0.0 && !((uint64_t)(u >> 1) < threshold_bits(beta, dE, 31)))
+        return si;
+    return s2;
+}
+
+/* s holds rows + 2 rows of L sites: row 0 is global row y0 - 1 (mod L), rows
+ * 1 .. rows are the owned global rows y0 .. y0 + rows - 1, row rows + 1 is
+ * global row y0 + rows (mod L).  Half-sweep of colour c at sweep t: every
+ * owned site with (x + y) & 1 == c (y the global row), row-major, in place,
+ * with its global random word; x is periodic, rows 0 and rows + 1 are only
+ * read.                                                                    */
+int oracle_slab_half_sweep(int8_t *s, int64_t rows, int64_t L, int64_t y0, int model,
+                           uint64_t seed, uint64_t t, int c, double beta, double delta)
+{
+    if (!s || rows < 1 || L < 2 || L % 2 != 0 || y0 < 0 || y0 + rows > L || (c != 0 && c != 1) ||
+        (model != ORACLE_ISING && model != ORACLE_BLUME_CAPEL))
+        return -1;
+    for (int64_t i = 1; i <= rows; ++i) {
+        const int64_t y = y0 + i - 1;
+        for (int64_t x = 0; x < L; ++x) {
+            if ((int)((x + y) & 1) != c)
+                continue;
+            const int64_t id = i * L + x;
+            const int h = s[i * L + dn1(x, L)] + s[i * L + up1(x, L)] + s[(i - 1) * L + x] +
+                          s[(i + 1) * L + x];
+            const uint64_t j = (uint64_t)(y * L + x) >> 1;
+            const uint32_t u = site_word(seed, j, (uint32_t)t, (uint32_t)c);
+            s[id] = (int8_t)metropolis_new_value(s[id], h, u, model, beta, delta);
+        }
+    }
+    return 0;
+}
+
+/* The owned rows' part of the observables of oracle_measure: B over the
+ * bonds of owned sites to +x and +y (the last owned row's +y neighbours are
+ * row rows + 1), M, Q, R[i] for owned row i, and C[x] summed over the owned
+ * rows only.                                                               */
+int oracle_slab_measure(const int8_t *s, int64_t rows, int64_t L, int64_t *bmq, int32_t *R,
+                        int32_t *C)
+{
+    if (!s || !bmq || rows < 1 || L < 1)
+        return -1;
+    int64_t B = 0, M = 0, Q = 0;
+    if (C)
+        for (int64_t x = 0; x < L; ++x)
+            C[x] = 0;
+    for (int64_t i = 1; i <= rows; ++i) {
+        int64_t row = 0;
+        for (int64_t x = 0; x < L; ++x) {
+            const int v = s[i * L + x];
+            B += (int64_t)v * (s[i * L + up1(x, L)] + s[(i + 1) * L + x]);
+            M += v;
+            Q += v * v;
+            row += v;
+            if (C)
+                C[x] += v;
+        }
+        if (R)
+            R[i - 1] = (int32_t)row;
+    }
+    bmq[0] = B;
+    bmq[1] = M;
+    bmq[2] = Q;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Correlation function along the lattice axes (Eq. (2)).                   */
 /* ------------------------------------------------------------------------ */
 

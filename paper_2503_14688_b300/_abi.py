@@ -67,6 +67,12 @@ class isg_result(ctypes.Structure):
                 ("t_done", ctypes.c_double), ("records", ctypes.c_int64)]
 
 
+class isg_slab_desc(ctypes.Structure):
+    _fields_ = [("model", ctypes.c_int32), ("L", ctypes.c_int64), ("y0", ctypes.c_int64),
+                ("rows", ctypes.c_int64), ("seed", ctypes.c_uint64), ("delta", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
 class isg_schedule(ctypes.Structure):
     _fields_ = [("n_pieces", ctypes.c_int64), ("t_start", ctypes.POINTER(ctypes.c_int64)),
                 ("beta", ctypes.POINTER(ctypes.c_double))]
@@ -129,6 +135,17 @@ PROTOTYPES = {
     "isg_server_clock": (_F64, [_P]),
     "isg_server_stats": (_I32, [_P, _F64P, ctypes.POINTER(ctypes.c_size_t),
                                 ctypes.POINTER(ctypes.c_size_t)]),
+    "isg_slab_edge_bytes": (ctypes.c_size_t, [_I32, _I64]),
+    "isg_slab_create": (_I32, [ctypes.POINTER(isg_slab_desc), ctypes.POINTER(_P)]),
+    "isg_slab_destroy": (None, [_P]),
+    "isg_slab_init_random": (_I32, [_P]),
+    "isg_slab_set": (_I32, [_P, _I8P, _I64]),
+    "isg_slab_get": (_I32, [_P, _I8P]),
+    "isg_slab_edges": (_I32, [_P, _I32, _P, _P]),
+    "isg_slab_set_halos": (_I32, [_P, _I32, _P, _P]),
+    "isg_slab_half_sweep": (_I32, [_P, _I32, _F64]),
+    "isg_slab_measure": (_I32, [_P, ctypes.POINTER(isg_obs)]),
+    "isg_slab_info": (_I32, [_P, _I64P, _I64P, _I64P, _I64P, _I32P]),
 }
 
 _lib = None

@@ -22,7 +22,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 CU_SOURCES = ["isg_kernels.cu", "isg_api.cu", "isg_noalloc.cu", "isg_ensemble.cu", "isg_server.cu",
-              "isg_sw.cu"]
+              "isg_sw.cu", "isg_slab.cu"]
 CPP_SOURCES = ["isg_host.cpp"]
 
 

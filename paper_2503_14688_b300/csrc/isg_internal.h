@@ -69,6 +69,21 @@ struct Planes {
     int32_t model;
 };
 
+// Device-side description of one row slab of an L x L lattice (domain
+// decomposition): the owned global rows y0 .. y0 + rows - 1.  Each plane
+// holds rows + 2 rows of W = L / 64 words (row 0: halo above, global row
+// y0 - 1 mod L; rows 1 .. rows: owned; row rows + 1: halo below, global row
+// y0 + rows mod L); planes are (rows + 2) W words apart, in the order of
+// Planes.
+struct SlabPlanes {
+    uint32_t *base;
+    int64_t L;
+    int64_t W;
+    int64_t rows;
+    int64_t y0;
+    int32_t model;
+};
+
 // Record layout in device memory: int64 [sweep, B, M, Q] then int32 R[L],
 // int32 C[L].
 inline size_t record_stride(int64_t L) { return 32 + 8 * (size_t)L; }
@@ -114,6 +129,17 @@ cudaError_t launch_half_sweep_multi(int model, int64_t L, uint32_t *const *plane
 cudaError_t launch_correlation(const Planes &pl, int nr, const int64_t *d_r, unsigned long long *d_out,
                                cudaStream_t st);
 cudaError_t launch_pack(const Planes &pl, const int8_t *d_spins, int32_t *d_bad, cudaStream_t st);
+// Row slabs (isg_slab.cu): half-sweep of the owned rows with the halo rows of
+// the neighbour colour; record (int64 [sweep, B, M, Q], int32 R[rows], int32
+// C[L]) of the owned rows, zeroed beforehand; hot start with global keys;
+// owned rows <-> rows x L bytes.
+cudaError_t launch_half_sweep_slab(const SlabPlanes &sp, int colour, const PhiloxLaunch &ph,
+                                   const IsingThr &ithr, const BcTable *btab, cudaStream_t st);
+cudaError_t launch_measure_slab(const SlabPlanes &sp, void *record, int64_t sweep, cudaStream_t st);
+cudaError_t launch_slab_init_random(const SlabPlanes &sp, const PhiloxLaunch &ph0, const PhiloxLaunch &ph1,
+                                    cudaStream_t st);
+cudaError_t launch_slab_convert(const SlabPlanes &sp, int8_t *d_spins, int to_planes, int32_t *d_bad,
+                                cudaStream_t st);
 cudaError_t launch_unpack_rect(const Planes &pl, int64_t y0, int64_t x0, int64_t h, int64_t w,
                                int8_t *d_out, cudaStream_t st);
 

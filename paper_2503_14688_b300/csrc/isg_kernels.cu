@@ -186,11 +186,18 @@ __global__ void k_init_uniform(Planes pl, int value)
 // up/same/down neighbour words in registers (each neighbour word is loaded
 // once per band plus two halo rows).
 // ---------------------------------------------------------------------------
-template <int V>
+//
+// kWrap = true: the whole periodic lattice (Li = L rows, rows wrap).
+// kWrap = false: a row slab of a larger lattice (domain decomposition): Li
+// rows starting at global row yg0, whose neighbour plane has one halo row
+// above row 0 and one below row Li - 1 (the neighbouring slabs' edge rows);
+// parity and random keys follow the global row.  Lx is the lattice side
+// (the row width in sites), which sets the Philox counter's row stride.
+template <int V, bool kWrap = true>
 __device__ __forceinline__ void ising_half_band(uint32_t g, uint32_t *__restrict__ tgt,
                                                 const uint32_t *__restrict__ nbr, uint32_t Li,
                                                 uint32_t Wi, int colour, int H, const PhiloxLaunch &pc,
-                                                const IsingThr &thr)
+                                                const IsingThr &thr, uint32_t yg0 = 0)
 {
     // threads enumerate (row band, V-word group) pairs, groups fastest, so
     // every block is full whatever the row width; rows and words fit 32 bits
@@ -201,23 +208,25 @@ __device__ __forceinline__ void ising_half_band(uint32_t g, uint32_t *__restrict
     if (y0 >= Li)
         return;
     const uint32_t y1 = y0 + H < Li ? y0 + H : Li;
-    const uint64_t qrow = (uint64_t)(Li / 8);
+    const uint64_t qrow = (uint64_t)(Wi * 8);  // L / 8 Philox counters per row
     // edge words of the two parities (periodic in the row)
     const uint32_t e_left = w0 == 0 ? Wi - 1 : w0 - 1;
     const uint32_t e_right = w0 + V == Wi ? 0 : w0 + V;
 
     const uint32_t *nrow = nbr + (uint64_t)y0 * Wi;
     uint32_t *trow = tgt + (uint64_t)y0 * Wi;
-    Words<V> U = load_words<V>(nbr + (uint64_t)(y0 == 0 ? Li - 1 : y0 - 1) * Wi + w0);
+    Words<V> U = load_words<V>(kWrap ? nbr + (uint64_t)(y0 == 0 ? Li - 1 : y0 - 1) * Wi + w0
+                                     : nrow - Wi + w0);
     Words<V> S = load_words<V>(nrow + w0);
     for (uint32_t y = y0; y < y1; ++y) {
-        const uint32_t *ndown = y + 1 == Li ? nbr : nrow + Wi;
+        const uint32_t *ndown = (kWrap && y + 1 == Li) ? nbr : nrow + Wi;
         const Words<V> D = load_words<V>(ndown + w0);
-        const int parity = (colour ^ (int)y) & 1;
+        const uint32_t yg = kWrap ? y : y + yg0;
+        const int parity = (colour ^ (int)yg) & 1;
         const uint32_t edge = __ldg(nrow + (parity == 0 ? e_left : e_right));
         const Words<V> X = side_words<V>(S, edge, parity);
         Words<V> T = load_words_rw<V>(trow + w0);
-        const uint64_t qy = (uint64_t)y * qrow + 8u * w0;
+        const uint64_t qy = (uint64_t)yg * qrow + 8u * w0;
 #pragma unroll
         for (int v = 0; v < V; ++v)
             T.v[v] = ising_word_update(T.v[v], U.v[v], D.v[v], S.v[v], X.v[v], qy + 8u * v, pc, thr);
@@ -265,13 +274,14 @@ __global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
 // site looks its threshold up in the table of BcTable, indexed by that byte
 // and its proposal bit, held in shared memory.
 // ---------------------------------------------------------------------------
-template <int V, bool kFull>
+// kWrap and yg0 as for ising_half_band; L is the number of rows swept.
+template <int V, bool kFull, bool kWrap = true>
 __device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ tn_plane,
                                              uint32_t *__restrict__ tp_plane,
                                              const uint32_t *__restrict__ nn_plane,
                                              const uint32_t *__restrict__ np_plane, int64_t L,
                                              int64_t W, int colour, int H, const PhiloxLaunch &pc,
-                                             const uint32_t *s_thr)
+                                             const uint32_t *s_thr, uint32_t yg0 = 0)
 {
     // rows and words fit 32 bits; row pointers advance by one row per step
     const uint32_t Li = (uint32_t)L, Wi = (uint32_t)W;
@@ -282,23 +292,24 @@ __device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ t
     if (y0 >= Li)
         return;
     const uint32_t y1 = y0 + H < Li ? y0 + H : Li;
-    const uint64_t qrow = (uint64_t)(Li / 8);
-    const uint32_t yu0 = y0 == 0 ? Li - 1 : y0 - 1;
+    const uint64_t qrow = (uint64_t)(Wi * 8);  // L / 8 Philox counters per row
     const uint32_t e_left = w0 == 0 ? Wi - 1 : w0 - 1;
     const uint32_t e_right = w0 + V == Wi ? 0 : w0 + V;
     const int64_t dpn = np_plane - nn_plane, dtp = tp_plane - tn_plane;  // occupancy -> sign plane
 
-    Words<V> Un = load_words<V>(nn_plane + (uint64_t)yu0 * Wi + w0);
-    Words<V> Up = load_words<V>(np_plane + (uint64_t)yu0 * Wi + w0);
     const uint32_t *nrow = nn_plane + (uint64_t)y0 * Wi;
+    const uint32_t *nup = kWrap ? nn_plane + (uint64_t)(y0 == 0 ? Li - 1 : y0 - 1) * Wi : nrow - Wi;
+    Words<V> Un = load_words<V>(nup + w0);
+    Words<V> Up = load_words<V>(nup + dpn + w0);
     uint32_t *trow = tn_plane + (uint64_t)y0 * Wi;
     Words<V> Sn = load_words<V>(nrow + w0);
     Words<V> Sp = load_words<V>(nrow + dpn + w0);
     for (uint32_t y = y0; y < y1; ++y) {
-        const uint32_t *ndown = y + 1 == Li ? nn_plane : nrow + Wi;
+        const uint32_t *ndown = (kWrap && y + 1 == Li) ? nn_plane : nrow + Wi;
         const Words<V> Dn = load_words<V>(ndown + w0);
         const Words<V> Dp = load_words<V>(ndown + dpn + w0);
-        const int parity = (colour ^ (int)y) & 1;
+        const uint32_t yg = kWrap ? y : y + yg0;
+        const int parity = (colour ^ (int)yg) & 1;
         const uint32_t *edge = nrow + (parity == 0 ? e_left : e_right);
         const Words<V> Xn = side_words<V>(Sn, __ldg(edge), parity);
         const Words<V> Xp = side_words<V>(Sp, __ldg(edge + dpn), parity);
@@ -308,7 +319,7 @@ __device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ t
         for (int v = 0; v < V; ++v) {
             const uint32_t nbn[4] = {Un.v[v], Dn.v[v], Sn.v[v], Xn.v[v]};
             const uint32_t nbp[4] = {Up.v[v], Dp.v[v], Sp.v[v], Xp.v[v]};
-            const uint64_t q0 = (uint64_t)y * qrow + 8u * (uint64_t)(w0 + v);
+            const uint64_t q0 = (uint64_t)yg * qrow + 8u * (uint64_t)(w0 + v);
             bc_word_update<kFull>(Tn.v[v], Tp.v[v], nbn, nbp, q0, pc, s_thr);
         }
         store_words<V>(trow + w0, Tn);
@@ -430,12 +441,16 @@ __device__ __forceinline__ void cc_zero(ColumnCounter &k)
         k.high[l] = 0;
 }
 
-template <int MODEL>
-__device__ __forceinline__ void measure_band(const Planes &pl, int H, int64_t *__restrict__ rec_hdr,
+// base: row 0 of plane 0; L rows of W words per plane, planes LW words
+// apart.  kWrap = true: the periodic lattice (L rows).  kWrap = false: a row
+// slab whose planes have a halo row above row 0 and below row L - 1, which
+// stand in for the wrap (its first global row must be a multiple of 16).
+template <int MODEL, bool kWrap = true>
+__device__ __forceinline__ void measure_band(const uint32_t *base, int64_t L, int64_t W, int64_t LW,
+                                             int H, int64_t *__restrict__ rec_hdr,
                                              int32_t *__restrict__ R, int32_t *__restrict__ C,
                                              int64_t sweep, int32_t *s_row)
 {
-    const int64_t L = pl.L, W = pl.W, LW = L * W;
     const int64_t y0 = (int64_t)blockIdx.y * H;
     const int rows = (int)((y0 + H < L ? y0 + H : L) - y0);  // a multiple of 16
     for (int i = threadIdx.x; i < rows; i += blockDim.x)
@@ -448,9 +463,9 @@ __device__ __forceinline__ void measure_band(const Planes &pl, int H, int64_t *_
     const bool active = w < W;
     const int64_t wc = active ? w : 0;
     // plane pointers: colour-0 / colour-1 sign planes (and occupancy planes)
-    const uint32_t *p0 = MODEL == 0 ? pl.base : pl.base + LW;
-    const uint32_t *p1 = MODEL == 0 ? pl.base + LW : pl.base + 3 * LW;
-    const uint32_t *n0 = pl.base, *n1 = pl.base + 2 * LW;  // Blume-Capel only
+    const uint32_t *p0 = MODEL == 0 ? base : base + LW;
+    const uint32_t *p1 = MODEL == 0 ? base + LW : base + 3 * LW;
+    const uint32_t *n0 = base, *n1 = base + 2 * LW;  // Blume-Capel only
     const int64_t wl = wc == 0 ? W - 1 : wc - 1, wr = wc + 1 == W ? 0 : wc + 1;
 
     int accB = 0, accM = 0, accQ = 0;
@@ -461,7 +476,7 @@ __device__ __forceinline__ void measure_band(const Planes &pl, int H, int64_t *_
         cc_zero(ce_m);
         cc_zero(co_m);
     }
-    const int64_t yup = y0 == 0 ? L - 1 : y0 - 1;
+    const int64_t yup = (kWrap && y0 == 0) ? L - 1 : y0 - 1;
     uint32_t Up = 0, Sp = 0, Un = 0, Sn = 0;
     if (active) {
         Up = __ldg(p0 + yup * W + wc);
@@ -483,7 +498,7 @@ __device__ __forceinline__ void measure_band(const Planes &pl, int H, int64_t *_
 #pragma unroll 1
         for (int g = 0; g < 4; ++g, t1 += 4 * W, t0 += 4 * W) {
             const int64_t yg = y0 + r0 + 4 * g;
-            const bool last = yg + 4 == L;  // row yg + 3 wraps to row 0
+            const bool last = kWrap && yg + 4 == L;  // row yg + 3 wraps to row 0
             uint32_t Tp[4], Dp[4], Ep[4], Tn[4], Dn[4], En[4];
             if (active) {
 #pragma unroll
@@ -599,7 +614,7 @@ __global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
               int32_t *__restrict__ C, int64_t sweep)
 {
     __shared__ int32_t s_row[kMeasureBand];
-    measure_band<MODEL>(pl, H, rec_hdr, R, C, sweep, s_row);
+    measure_band<MODEL>(pl.base, pl.L, pl.W, pl.L * pl.W, H, rec_hdr, R, C, sweep, s_row);
 }
 
 // Records of many lattices of one side L in one launch (the ensemble's
@@ -616,14 +631,9 @@ __global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
 {
     __shared__ int32_t s_row[kMeasureBand];
     const int r = blockIdx.z;
-    Planes pl;
-    pl.base = a.planes[r];
-    pl.L = L;
-    pl.W = L / 64;
-    pl.model = MODEL;
     int64_t *hdr = reinterpret_cast<int64_t *>(a.rec[r]);
     int32_t *R = reinterpret_cast<int32_t *>(hdr + 4);
-    measure_band<MODEL>(pl, H, hdr, R, R + L, sweep, s_row);
+    measure_band<MODEL>(a.planes[r], L, L / 64, L * (L / 64), H, hdr, R, R + L, sweep, s_row);
 }
 
 // Zero the record slots of a multi-lattice measure launch.
@@ -633,6 +643,125 @@ __global__ void k_zero_records(const __grid_constant__ MeasureMultiArgs a, int n
         uint32_t *p = reinterpret_cast<uint32_t *>(a.rec[r]);
         for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < words; i += gridDim.x * blockDim.x)
             p[i] = 0u;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row slabs of a lattice (domain decomposition, Introduction: the paper
+// splits one lattice over many GPUs).  A slab's planes hold rows + 2 rows of
+// W words each: row 0 is the halo above (global row y0 - 1, periodic), rows
+// 1 .. rows the owned rows y0 .. y0 + rows - 1, row rows + 1 the halo below
+// (global row y0 + rows).  The half-sweep and the observables are the band
+// walks above with the halo rows in place of the periodic wrap and the
+// global row for parity and random keys.
+// ---------------------------------------------------------------------------
+template <int V>
+__global__ void __launch_bounds__(kSweepThreads, V == 4 ? kSweepMinBlocks : 8)
+    k_ising_half_slab(uint32_t *__restrict__ tgt, const uint32_t *__restrict__ nbr, int64_t rows,
+                      int64_t W, int colour, int H, PhiloxLaunch pc, IsingThr thr, uint32_t yg0)
+{
+    ising_half_band<V, false>(blockIdx.x * blockDim.x + threadIdx.x, tgt, nbr, (uint32_t)rows,
+                              (uint32_t)W, colour, H, pc, thr, yg0);
+}
+
+template <int V, bool kFull>
+__global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
+    k_bc_half_slab(uint32_t *__restrict__ tn_plane, uint32_t *__restrict__ tp_plane,
+                   const uint32_t *__restrict__ nn_plane, const uint32_t *__restrict__ np_plane,
+                   int64_t rows, int64_t W, int colour, int H, PhiloxLaunch pc, BcTable tab,
+                   uint32_t yg0)
+{
+    __shared__ uint32_t s_thr[kBcTableSize];
+    for (int i = threadIdx.x; i < kBcTableSize; i += blockDim.x)
+        s_thr[i] = tab.thr[i];
+    __syncthreads();
+    bc_half_band<V, kFull, false>((int64_t)blockIdx.x * blockDim.x + threadIdx.x, tn_plane, tp_plane,
+                                  nn_plane, np_plane, rows, W, colour, H, pc, s_thr, yg0);
+}
+
+template <int MODEL>
+__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
+    k_measure_slab(const uint32_t *base, int64_t rows, int64_t W, int H, int64_t *__restrict__ rec_hdr,
+                   int32_t *__restrict__ R, int32_t *__restrict__ C, int64_t sweep)
+{
+    __shared__ int32_t s_row[kMeasureBand];
+    measure_band<MODEL, false>(base + W, rows, W, (rows + 2) * W, H, rec_hdr, R, C, sweep, s_row);
+}
+
+// Hot start of the owned rows (global keys) and byte <-> plane conversion of
+// the owned rows.  One thread per word of an owned row of either colour.
+__global__ void k_slab_init_random(SlabPlanes sp, PhiloxLaunch ph0, PhiloxLaunch ph1)
+{
+    const int64_t words = sp.rows * sp.W;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= 2 * words)
+        return;
+    const int c = gid >= words;
+    const int64_t wi = c ? gid - words : gid;  // local row * W + w
+    const int64_t yl = wi / sp.W, w = wi - yl * sp.W;
+    const PhiloxLaunch &pc = c ? ph1 : ph0;
+    const uint64_t q0 = (uint64_t)(sp.y0 + yl) * (uint64_t)(sp.L / 8) + 8u * (uint64_t)w;
+    const PhiloxWordPart wp = philox_word_part(pc, (uint32_t)(q0 >> 32));
+    uint32_t bits_n = 0, bits_p = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        uint32_t r[4];
+        philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int b = 4 * i + k;
+            if (sp.model == 0) {
+                bits_p |= (r[k] >> 31) << b;
+            } else {
+                const uint32_t v = (uint32_t)(((uint64_t)r[k] * 3u) >> 32);  // 0,1,2 -> s = v-1
+                bits_n |= (uint32_t)(v != 1) << b;
+                bits_p |= (uint32_t)(v == 2) << b;
+            }
+        }
+    }
+    const int64_t PS = (sp.rows + 2) * sp.W, off = sp.W + wi;
+    if (sp.model == 0) {
+        sp.base[(int64_t)c * PS + off] = bits_p;
+    } else {
+        sp.base[(int64_t)(2 * c) * PS + off] = bits_n;
+        sp.base[(int64_t)(2 * c + 1) * PS + off] = bits_p;
+    }
+}
+
+// s: rows x L bytes (row-major, owned rows); to_planes = 1 packs s into the
+// planes (flagging values outside the model's set), 0 unpacks.
+__global__ void k_slab_convert(SlabPlanes sp, int8_t *s, int to_planes, int32_t *bad)
+{
+    const int64_t words = sp.rows * sp.W;
+    const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gid >= 2 * words)
+        return;
+    const int c = gid >= words;
+    const int64_t wi = c ? gid - words : gid;
+    const int64_t yl = wi / sp.W, w = wi - yl * sp.W;
+    const int par = (c ^ (int)((sp.y0 + yl) & 1)) & 1;
+    const int64_t PS = (sp.rows + 2) * sp.W, off = sp.W + wi;
+    uint32_t *pn = sp.base + (int64_t)(sp.model == 0 ? c : 2 * c) * PS + off;
+    uint32_t *pp = sp.base + (int64_t)(sp.model == 0 ? c : 2 * c + 1) * PS + off;
+    int8_t *row = s + yl * sp.L;
+    if (to_planes) {
+        uint32_t bn = 0, bp = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int v = row[2 * (32 * w + b) + par];
+            if (sp.model == 0 ? (v != 1 && v != -1) : (v < -1 || v > 1))
+                atomicExch(bad, 1);
+            bn |= (uint32_t)(v != 0) << b;
+            bp |= (uint32_t)(v > 0) << b;
+        }
+        *pp = bp;
+        if (sp.model != 0)
+            *pn = bn;
+    } else {
+        const uint32_t bp = *pp, bn = sp.model == 0 ? ~0u : *pn;
+        for (int b = 0; b < 32; ++b) {
+            const int on = (bn >> b) & 1, up = (bp >> b) & 1;
+            row[2 * (32 * w + b) + par] = (int8_t)(sp.model == 0 ? (up ? 1 : -1) : (on ? (up ? 1 : -1) : 0));
+        }
     }
 }
 
@@ -1043,6 +1172,83 @@ cudaError_t launch_measure_multi(int model, int64_t L, uint32_t *const *planes, 
             return e;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_half_sweep_slab(const SlabPlanes &sp, int colour, const PhiloxLaunch &ph,
+                                   const IsingThr &ithr, const BcTable *btab, cudaStream_t st)
+{
+    const int64_t PS = (sp.rows + 2) * sp.W;
+    const uint32_t yg0 = (uint32_t)sp.y0;
+    if (sp.model == 0) {
+        uint32_t *tgt = sp.base + (int64_t)colour * PS + sp.W;
+        const uint32_t *nbr = sp.base + (int64_t)(1 - colour) * PS + sp.W;
+        const int V = words_per_thread(sp.rows, sp.W, 4, kSweepMinBlocks, kSweepThreads, 1);
+        const int64_t tpr = sp.W / V;
+        const int H = sweep_band(sp.rows, tpr);
+        const unsigned blocks = sweep_blocks(sp.rows, tpr, H);
+        if (V == 4)
+            k_ising_half_slab<4><<<blocks, kSweepThreads, 0, st>>>(tgt, nbr, sp.rows, sp.W, colour, H, ph, ithr, yg0);
+        else if (V == 2)
+            k_ising_half_slab<2><<<blocks, kSweepThreads, 0, st>>>(tgt, nbr, sp.rows, sp.W, colour, H, ph, ithr, yg0);
+        else
+            k_ising_half_slab<1><<<blocks, kSweepThreads, 0, st>>>(tgt, nbr, sp.rows, sp.W, colour, H, ph, ithr, yg0);
+        return cudaGetLastError();
+    }
+    uint32_t *tn = sp.base + (int64_t)(2 * colour) * PS + sp.W;
+    uint32_t *tp = tn + PS;
+    const uint32_t *nn = sp.base + (int64_t)(2 * (1 - colour)) * PS + sp.W;
+    const uint32_t *np = nn + PS;
+    const int V = words_per_thread(sp.rows, sp.W, 2, kBcMinBlocks, kBcThreads, 1) == 2 ? 2 : 1;
+    const int64_t tpr = sp.W / V;
+    const int H = sweep_band(sp.rows, tpr, kBcMinBlocks, kBcThreads, 2);
+    const int64_t threads = tpr * ((sp.rows + H - 1) / H);
+    const unsigned blocks = (unsigned)((threads + kBcThreads - 1) / kBcThreads);
+    if (V == 2) {
+        if (btab->full)
+            k_bc_half_slab<2, true><<<blocks, kBcThreads, 0, st>>>(tn, tp, nn, np, sp.rows, sp.W, colour, H, ph, *btab, yg0);
+        else
+            k_bc_half_slab<2, false><<<blocks, kBcThreads, 0, st>>>(tn, tp, nn, np, sp.rows, sp.W, colour, H, ph, *btab, yg0);
+    } else {
+        if (btab->full)
+            k_bc_half_slab<1, true><<<blocks, kBcThreads, 0, st>>>(tn, tp, nn, np, sp.rows, sp.W, colour, H, ph, *btab, yg0);
+        else
+            k_bc_half_slab<1, false><<<blocks, kBcThreads, 0, st>>>(tn, tp, nn, np, sp.rows, sp.W, colour, H, ph, *btab, yg0);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_measure_slab(const SlabPlanes &sp, void *record, int64_t sweep, cudaStream_t st)
+{
+    int64_t *hdr = reinterpret_cast<int64_t *>(record);
+    int32_t *R = reinterpret_cast<int32_t *>(hdr + 4);
+    int32_t *C = R + sp.rows;
+    // band height: a multiple of 16 (rows is one), as in launch_measure
+    const int64_t bx = (sp.W + kMeasureThreads - 1) / kMeasureThreads;
+    int64_t H = sp.rows < kMeasureBand ? sp.rows : kMeasureBand;
+    while (H % 32 == 0 && bx * ((sp.rows + H - 1) / H) < 148 * 4)
+        H >>= 1;
+    const dim3 grid((unsigned)bx, (unsigned)((sp.rows + H - 1) / H));
+    if (sp.model == 0)
+        k_measure_slab<0><<<grid, kMeasureThreads, 0, st>>>(sp.base, sp.rows, sp.W, (int)H, hdr, R, C, sweep);
+    else
+        k_measure_slab<1><<<grid, kMeasureThreads, 0, st>>>(sp.base, sp.rows, sp.W, (int)H, hdr, R, C, sweep);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab_init_random(const SlabPlanes &sp, const PhiloxLaunch &ph0, const PhiloxLaunch &ph1,
+                                    cudaStream_t st)
+{
+    const int64_t n = 2 * sp.rows * sp.W;
+    k_slab_init_random<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sp, ph0, ph1);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_slab_convert(const SlabPlanes &sp, int8_t *d_spins, int to_planes, int32_t *d_bad,
+                                cudaStream_t st)
+{
+    const int64_t n = 2 * sp.rows * sp.W;
+    k_slab_convert<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(sp, d_spins, to_planes, d_bad);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_correlation(const Planes &pl, int nr, const int64_t *d_r, unsigned long long *d_out,

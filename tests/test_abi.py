@@ -66,6 +66,16 @@ def test_invalid_arguments_rejected_before_any_device_work(abi):
     assert lib.isg_sweep(None, 1, None, 0.4, 0) == abi.ISG_ERR_INVALID
     assert lib.isg_sweep(None, 1, None, -1.0, 0) == abi.ISG_ERR_INVALID
     lib.isg_lattice_destroy(None)  # NULL-safe
+    # row slabs: offsets and heights in multiples of 16, inside the lattice
+    for y0, rows in [(8, 16), (0, 24), (0, 0), (112, 32), (-16, 32)]:
+        d = abi.isg_slab_desc(model=0, L=128, y0=y0, rows=rows, seed=1)
+        assert lib.isg_slab_create(ctypes.byref(d), ctypes.byref(h)) == abi.ISG_ERR_INVALID
+        assert not h.value
+    assert lib.isg_slab_edge_bytes(abi.ISG_ISING, 1024) == 1024 // 16
+    assert lib.isg_slab_edge_bytes(abi.ISG_BLUME_CAPEL, 1024) == 1024 // 8
+    assert lib.isg_slab_edge_bytes(abi.ISG_ISING, 100) == 0
+    assert lib.isg_slab_half_sweep(None, 0, 0.4) == abi.ISG_ERR_INVALID
+    lib.isg_slab_destroy(None)  # NULL-safe
 
 
 def test_without_gpu_create_reports_unsupported(abi):
