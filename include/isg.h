@@ -310,13 +310,19 @@ isg_status isg_ensemble_autotune(isg_ensemble *ens, int64_t sweeps, int32_t *thr
  * chunk_sweeps sweeps -- lattices that fit in shared memory (Ising L <= 1280,
  * Blume-Capel L <= 896) together in one persistent launch, larger ones on
  * streams of their own, overlapping it.  A result does not depend on what
- * else ran or where chunks were cut (per-site keying).
+ * else ran or where chunks were cut (per-site keying).  Requests leave the
+ * schedule when done, when cancelled, when their deadline passes, or when
+ * their allocation or a launch fails; each outcome is a state of
+ * isg_result, and a failure never stops the others.
  * ------------------------------------------------------------------------- */
 typedef struct isg_server isg_server;
 
 #define ISG_REQ_QUEUED 0
 #define ISG_REQ_RUNNING 1
 #define ISG_REQ_DONE 2
+#define ISG_REQ_CANCELLED 3  /* isg_server_cancel before it finished           */
+#define ISG_REQ_EXPIRED 4    /* its deadline passed before it finished          */
+#define ISG_REQ_FAILED 5     /* its allocation or a launch failed (error field) */
 
 typedef struct {
     size_t hbm_budget;      /* device bytes requests may hold (capped at the free
@@ -328,7 +334,7 @@ typedef struct {
 
 typedef struct {
     int32_t model;
-    int64_t L;              /* a valid side and a multiple of 256                */
+    int64_t L;              /* a valid side (a multiple of 64)                   */
     uint64_t seed;
     double delta;           /* Blume-Capel crystal field                         */
     int64_t n_sweeps;       /* >= 1                                              */
@@ -341,6 +347,9 @@ typedef struct {
     int32_t keep_result;    /* 1: keep lattice and records until
                                isg_server_release; 0: free them when done        */
     double arrival_time;    /* seconds on the server clock; < 0 = now            */
+    double deadline;        /* seconds on the server clock by which it must be
+                               done; a request still queued or running after it
+                               is dropped (ISG_REQ_EXPIRED); <= 0 = none         */
 } isg_request;
 
 typedef struct {
@@ -350,14 +359,24 @@ typedef struct {
     double t_arrival, t_admit, t_done;  /* server clock (s); t_done from a CUDA
                                event after the request's last device work        */
     int64_t records;        /* periodic records not yet read                     */
+    int32_t error;          /* ISG_REQ_FAILED: the status that failed it (e.g.
+                               ISG_ERR_OOM from its allocation); else ISG_OK     */
 } isg_result;
 
 isg_status isg_server_create(const isg_server_desc *desc, isg_server **out);
 void isg_server_destroy(isg_server *srv);  /* waits for the device; NULL accepted */
 /* Queue a request; *id identifies it.  ISG_ERR_OOM if it can never fit. */
 isg_status isg_server_submit(isg_server *srv, const isg_request *req, uint64_t *id);
-/* One scheduling round (asynchronous device work); counts after it. */
+/* One scheduling round (asynchronous device work); counts after it.  A
+ * request whose allocation or launch fails is failed alone (ISG_REQ_FAILED,
+ * its memory freed); the others go on. */
 isg_status isg_server_step(isg_server *srv, int32_t *active, int32_t *queued);
+/* Take a queued or running request out of the schedule: it never starts, or
+ * stops after the chunk already queued on the device (the call waits for
+ * that chunk), and its device memory is freed; state ISG_REQ_CANCELLED.
+ * ISG_ERR_INVALID for an unknown request or one that already left the
+ * schedule (done, cancelled, expired, failed). */
+isg_status isg_server_cancel(isg_server *srv, uint64_t id);
 /* Rounds until every submitted request is done (waits for arrivals). */
 isg_status isg_server_drain(isg_server *srv);
 isg_status isg_server_poll(isg_server *srv, uint64_t id, isg_result *out);
@@ -499,6 +518,19 @@ isg_status isg_sw_labels(isg_lattice *lat, int32_t *out);
 /* Swendsen-Wang iterations done on this lattice (reset by the init calls,
  * kept by isg_save / isg_load). */
 isg_status isg_sw_iterations(const isg_lattice *lat, int64_t *count);
+
+/* Fault injection, for testing callers' and the library's error paths on
+ * the host (no device fault is ever raised).  what = ISG_INJECT_ALLOC: the
+ * `after`-th device allocation the library makes from now on (counting this
+ * process's calls of every object) fails as out of memory -- nothing is
+ * allocated and the call reports ISG_ERR_OOM after freeing what it had
+ * allocated.  what = ISG_INJECT_LAUNCH: the `after`-th sweep kernel launch
+ * (single-lattice, slab, multi-lattice or persistent ensemble / server
+ * launch) is skipped and the call reports ISG_ERR_CUDA.  Each injection
+ * fires once; after = 0 disarms it.  Process-wide, thread-safe. */
+#define ISG_INJECT_ALLOC 1
+#define ISG_INJECT_LAUNCH 2
+isg_status isg_debug_inject(int32_t what, int64_t after);
 
 /* Energy per spin (-B + Delta Q) / L^2 of one record. */
 double isg_energy_density(const isg_obs *obs, int64_t L, double delta);

@@ -20,6 +20,8 @@ ISG_ERR_UNSUPPORTED = -6
 ISG_NOALLOC_MAX_L = 1 << 18
 ISG_SW_MAX_L = 32768
 ISG_REQ_QUEUED, ISG_REQ_RUNNING, ISG_REQ_DONE = 0, 1, 2
+ISG_REQ_CANCELLED, ISG_REQ_EXPIRED, ISG_REQ_FAILED = 3, 4, 5
+ISG_INJECT_ALLOC, ISG_INJECT_LAUNCH = 1, 2
 ISG_ISING = 0
 ISG_BLUME_CAPEL = 1
 
@@ -57,14 +59,16 @@ class isg_request(ctypes.Structure):
                 ("delta", ctypes.c_double), ("n_sweeps", ctypes.c_int64),
                 ("n_pieces", ctypes.c_int64), ("t_start", ctypes.POINTER(ctypes.c_int64)),
                 ("beta", ctypes.POINTER(ctypes.c_double)), ("record_every", ctypes.c_int64),
-                ("keep_result", ctypes.c_int32), ("arrival_time", ctypes.c_double)]
+                ("keep_result", ctypes.c_int32), ("arrival_time", ctypes.c_double),
+                ("deadline", ctypes.c_double)]
 
 
 class isg_result(ctypes.Structure):
     _fields_ = [("state", ctypes.c_int32), ("sweeps_done", ctypes.c_int64),
                 ("B", ctypes.c_int64), ("M", ctypes.c_int64), ("Q", ctypes.c_int64),
                 ("t_arrival", ctypes.c_double), ("t_admit", ctypes.c_double),
-                ("t_done", ctypes.c_double), ("records", ctypes.c_int64)]
+                ("t_done", ctypes.c_double), ("records", ctypes.c_int64),
+                ("error", ctypes.c_int32)]
 
 
 class isg_slab_desc(ctypes.Structure):
@@ -127,6 +131,8 @@ PROTOTYPES = {
     "isg_server_destroy": (None, [_P]),
     "isg_server_submit": (_I32, [_P, ctypes.POINTER(isg_request), _U64P]),
     "isg_server_step": (_I32, [_P, _I32P, _I32P]),
+    "isg_server_cancel": (_I32, [_P, _U64]),
+    "isg_debug_inject": (_I32, [_I32, _I64]),
     "isg_server_drain": (_I32, [_P]),
     "isg_server_poll": (_I32, [_P, _U64, ctypes.POINTER(isg_result)]),
     "isg_server_read_records": (_I32, [_P, _U64, ctypes.POINTER(isg_obs), _I64, _I64P]),

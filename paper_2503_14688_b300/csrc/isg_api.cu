@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -59,6 +60,42 @@ bool valid_beta(double b) { return !std::isnan(b) && b >= 0.0; }
 }  // namespace
 
 namespace isg {
+
+namespace {
+// armed injections: the count of events still to pass before the failing
+// one (0 = disarmed)
+std::atomic<int64_t> g_inject_alloc{0}, g_inject_launch{0};
+
+bool take(std::atomic<int64_t> &counter)
+{
+    int64_t v = counter.load();
+    while (v > 0) {
+        if (counter.compare_exchange_weak(v, v - 1))
+            return v == 1;
+    }
+    return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc_raw(void **p, size_t bytes)
+{
+    if (take(g_inject_alloc)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t dev_malloc_async_raw(void **p, size_t bytes, cudaStream_t st)
+{
+    if (take(g_inject_alloc)) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
+bool injected_launch_failure() { return take(g_inject_launch); }
 
 int32_t report_error(int32_t code, const char *fmt, ...)
 {
@@ -224,6 +261,19 @@ isg_status sweep_impl(isg_lattice *lat, int64_t n, const double *betas, double b
 
 extern "C" {
 
+isg_status isg_debug_inject(int32_t what, int64_t after)
+{
+    if (after < 0)
+        return fail(ISG_ERR_INVALID, "after must be >= 0");
+    if (what == ISG_INJECT_ALLOC)
+        isg::g_inject_alloc.store(after);
+    else if (what == ISG_INJECT_LAUNCH)
+        isg::g_inject_launch.store(after);
+    else
+        return fail(ISG_ERR_INVALID, "unknown injection %d", what);
+    return ISG_OK;
+}
+
 size_t isg_lattice_bytes(int32_t model, int64_t L)
 {
     if (!valid_L(model, L))
@@ -271,13 +321,13 @@ isg_status isg_lattice_create(const isg_lattice_desc *desc, isg_lattice **out)
         lat->planes = (uint32_t *)desc->device_buf;
         lat->owns_planes = false;
     } else {
-        e = cudaMalloc(&lat->planes, bytes);
+        e = dev_malloc(&lat->planes, bytes);
         lat->owns_planes = true;
     }
     if (e == cudaSuccess)
-        e = cudaMalloc(&lat->records, lat->rec_stride * (size_t)(lat->rec_cap + 1));
+        e = dev_malloc(&lat->records, lat->rec_stride * (size_t)(lat->rec_cap + 1));
     if (e == cudaSuccess)
-        e = cudaMalloc(&lat->d_flag, sizeof(int32_t));
+        e = dev_malloc(&lat->d_flag, sizeof(int32_t));
     if (e != cudaSuccess) {
         isg_status s = cuda_fail(e, "lattice allocation");
         cudaGetLastError();
@@ -340,7 +390,7 @@ isg_status isg_lattice_set(isg_lattice *lat, const int8_t *host, int64_t t)
         return fail(ISG_ERR_INVALID, "sweep index %lld out of range", (long long)t);
     const size_t n = (size_t)lat->L * (size_t)lat->L;
     int8_t *d = nullptr;
-    ISG_CUDA(cudaMallocAsync(&d, n, lat->stream), "staging allocation");
+    ISG_CUDA(dev_malloc_async(&d, n, lat->stream), "staging allocation");
     isg_status s = ISG_OK;
     int32_t bad = 0;
     cudaError_t e = cudaMemcpyAsync(d, host, n, cudaMemcpyHostToDevice, lat->stream);
@@ -373,7 +423,7 @@ isg_status isg_lattice_get_rect(isg_lattice *lat, int64_t y0, int64_t x0, int64_
     if (n == 0)
         return ISG_OK;
     int8_t *d = nullptr;
-    ISG_CUDA(cudaMallocAsync(&d, n, lat->stream), "staging allocation");
+    ISG_CUDA(dev_malloc_async(&d, n, lat->stream), "staging allocation");
     cudaError_t e = launch_unpack_rect(planes_of(lat), y0 % lat->L, x0 % lat->L, h, w, d, lat->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, d, n, cudaMemcpyDeviceToHost, lat->stream);
@@ -610,8 +660,8 @@ isg_status isg_correlation(isg_lattice *lat, int64_t nr, const int64_t *r, int64
         return ISG_OK;
     int64_t *d_r = nullptr;
     unsigned long long *d_out = nullptr;
-    ISG_CUDA(cudaMallocAsync(&d_r, sizeof(int64_t) * nr, lat->stream), "staging allocation");
-    cudaError_t e = cudaMallocAsync(&d_out, sizeof(unsigned long long) * 2 * nr, lat->stream);
+    ISG_CUDA(dev_malloc_async(&d_r, sizeof(int64_t) * nr, lat->stream), "staging allocation");
+    cudaError_t e = dev_malloc_async(&d_out, sizeof(unsigned long long) * 2 * nr, lat->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_r, r, sizeof(int64_t) * nr, cudaMemcpyHostToDevice, lat->stream);
     if (e == cudaSuccess)
@@ -670,7 +720,7 @@ isg_status isg_swendsen_wang(isg_lattice *lat, double beta)
         return fail(ISG_ERR_INVALID, "Swendsen-Wang iteration count exceeds 2^32");
     const int64_t n = lat->L * lat->L;
     if (!lat->sw_labels)
-        ISG_CUDA(cudaMalloc(&lat->sw_labels, sizeof(uint32_t) * (size_t)n), "label allocation");
+        ISG_CUDA(dev_malloc(&lat->sw_labels, sizeof(uint32_t) * (size_t)n), "label allocation");
     PhiloxLaunch px, py, pc;
     const uint32_t k = (uint32_t)lat->sw_count;
     philox_launch_consts(lat->seed, k, 4u, &px);

@@ -133,10 +133,10 @@ isg_status ensure_tables(isg_ensemble *e, int64_t n)
     cudaStreamSynchronize(e->stream);
     free_tables(e);
     const int64_t cap = std::max<int64_t>(n, 64);
-    ECUDA(cudaMalloc(&e->d_ithr, sizeof(IsingThr) * cap), "threshold table");
+    ECUDA(dev_malloc(&e->d_ithr, sizeof(IsingThr) * cap), "threshold table");
     ECUDA(cudaMallocHost(&e->h_ithr, sizeof(IsingThr) * cap), "threshold table (host)");
     if (e->any_bc) {
-        ECUDA(cudaMalloc(&e->d_btab, sizeof(BcTable) * cap), "threshold table");
+        ECUDA(dev_malloc(&e->d_btab, sizeof(BcTable) * cap), "threshold table");
         ECUDA(cudaMallocHost(&e->h_btab, sizeof(BcTable) * cap), "threshold table (host)");
     }
     e->thr_cap = cap;
@@ -189,6 +189,8 @@ isg_status queue_sweeps(isg_ensemble *e, int64_t n, int64_t record_every, int64_
         ECUDA(cudaMemcpyAsync(e->d_args, e->h_args, sizeof(EnsArgs), cudaMemcpyHostToDevice, st),
               "ensemble args");
         ECUDA(cudaMemsetAsync(e->d_counter, 0, sizeof(int32_t), st), "work counter");
+        if (injected_launch_failure())
+            return ecuda(cudaErrorLaunchFailure, "ensemble launch");
         k_ensemble<<<e->blocks, e->threads, e->smem, st>>>(e->d_args);
         ECUDA(cudaGetLastError(), "ensemble launch");
     }
@@ -273,13 +275,13 @@ isg_status isg_ensemble_create(const isg_ensemble_desc *d, isg_ensemble **out)
         roff += record_stride(e->L[r]);
     }
     e->row_bytes = (roff + 255) & ~(uint64_t)255;
-    cudaError_t err = cudaMalloc(&e->planes, off);
+    cudaError_t err = dev_malloc(&e->planes, off);
     if (err == cudaSuccess)
-        err = cudaMalloc(&e->rec_ring, e->row_bytes * (uint64_t)e->rec_cap);
+        err = dev_malloc(&e->rec_ring, e->row_bytes * (uint64_t)e->rec_cap);
     if (err == cudaSuccess)
-        err = cudaMalloc(&e->d_counter, sizeof(int32_t));
+        err = dev_malloc(&e->d_counter, sizeof(int32_t));
     if (err == cudaSuccess)
-        err = cudaMalloc(&e->d_args, sizeof(EnsArgs));
+        err = dev_malloc(&e->d_args, sizeof(EnsArgs));
     if (err == cudaSuccess)
         err = cudaMallocHost(&e->h_args, sizeof(EnsArgs));
     if (err != cudaSuccess)
@@ -338,9 +340,9 @@ isg_status isg_ensemble_create(const isg_ensemble_desc *d, isg_ensemble **out)
         items[r].model = e->model[r];
         items[r].own = 0;
     }
-    err = cudaMalloc(&e->d_items, sizeof(EnsItem) * d->n);
+    err = dev_malloc(&e->d_items, sizeof(EnsItem) * d->n);
     if (err == cudaSuccess && !order.empty())
-        err = cudaMalloc(&e->d_order, sizeof(int32_t) * order.size());
+        err = dev_malloc(&e->d_order, sizeof(int32_t) * order.size());
     if (err == cudaSuccess)
         err = cudaMemcpy(e->d_items, items.data(), sizeof(EnsItem) * d->n, cudaMemcpyHostToDevice);
     if (err == cudaSuccess && !order.empty())
@@ -552,7 +554,7 @@ isg_status isg_ensemble_get(isg_ensemble *e, int64_t r, int8_t *out)
     const Planes pl = replica_planes(e, r);
     const size_t nbytes = (size_t)pl.L * (size_t)pl.L;
     int8_t *d = nullptr;
-    ECUDA(cudaMallocAsync(&d, nbytes, e->stream), "staging allocation");
+    ECUDA(dev_malloc_async(&d, nbytes, e->stream), "staging allocation");
     cudaError_t err = launch_unpack_rect(pl, 0, 0, pl.L, pl.L, d, e->stream);
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(out, d, nbytes, cudaMemcpyDeviceToHost, e->stream);
@@ -589,8 +591,8 @@ isg_status isg_ensemble_autotune(isg_ensemble *e, int64_t sweeps, int32_t *threa
         total = std::max<size_t>(total, e->plane_off[r] + isg_lattice_bytes(e->model[r], e->L[r]));
     uint8_t *copy = nullptr;
     EnsItem *items = nullptr;
-    ECUDA(cudaMalloc(&copy, total), "autotune copy");
-    cudaError_t err = cudaMalloc(&items, sizeof(EnsItem) * e->n);
+    ECUDA(dev_malloc(&copy, total), "autotune copy");
+    cudaError_t err = dev_malloc(&items, sizeof(EnsItem) * e->n);
     std::vector<EnsItem> h(e->n);
     if (err == cudaSuccess)
         err = cudaMemcpy(h.data(), e->d_items, sizeof(EnsItem) * e->n, cudaMemcpyDeviceToHost);

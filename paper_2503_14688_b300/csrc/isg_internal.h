@@ -97,6 +97,27 @@ double xi_integral_fp64(int64_t n, const double *r, const double *c, double r_cu
 // Swendsen-Wang bond threshold rne(2^32 (1 - e^{-2 beta})), 2^32 = always.
 uint64_t sw_threshold(double beta);
 
+// ---- fault injection (isg_debug_inject, isg_api.cu) ----
+// Every device allocation of the library goes through dev_malloc /
+// dev_malloc_async, and every kernel launch of the sweep paths first asks
+// injected_launch_failure(): an armed injection makes the k-th such event
+// fail -- the allocation reports cudaErrorMemoryAllocation without
+// allocating, the launch is skipped and reports cudaErrorLaunchFailure -- so
+// the error paths can be tested on the host, with no device fault.
+cudaError_t dev_malloc_raw(void **p, size_t bytes);
+cudaError_t dev_malloc_async_raw(void **p, size_t bytes, cudaStream_t st);
+bool injected_launch_failure();
+template <class T>
+cudaError_t dev_malloc(T **p, size_t bytes)
+{
+    return dev_malloc_raw(reinterpret_cast<void **>(p), bytes);
+}
+template <class T>
+cudaError_t dev_malloc_async(T **p, size_t bytes, cudaStream_t st)
+{
+    return dev_malloc_async_raw(reinterpret_cast<void **>(p), bytes, st);
+}
+
 // ---- error reporting shared by the C-ABI files (isg_api.cu) ----
 // Stores a printf-style message for isg_last_error() and returns code.
 int32_t report_error(int32_t code, const char *fmt, ...);

@@ -1053,6 +1053,8 @@ int words_per_thread(int64_t L, int64_t W, int vmax, int blocks_per_sm, int thre
 cudaError_t launch_half_sweep(const Planes &pl, int colour, const PhiloxLaunch &ph,
                               const IsingThr &ithr, const BcTable *btab, cudaStream_t st)
 {
+    if (injected_launch_failure())
+        return cudaErrorLaunchFailure;
     if (pl.model == 0) {
         const int V = words_per_thread(pl.L, pl.W, 4, kSweepMinBlocks, kSweepThreads, 1);
         if (V == 4)
@@ -1074,6 +1076,8 @@ cudaError_t launch_half_sweep_multi(int model, int64_t L, uint32_t *const *plane
                                     const BcTable *btab, cudaStream_t st)
 {
     const int64_t W = L / 64;
+    if (injected_launch_failure())
+        return cudaErrorLaunchFailure;
     for (int i0 = 0; i0 < n; i0 += kMultiMax) {
         const int m = n - i0 < kMultiMax ? n - i0 : kMultiMax;
         MultiArgs a;
@@ -1177,6 +1181,8 @@ cudaError_t launch_measure_multi(int model, int64_t L, uint32_t *const *planes, 
 cudaError_t launch_half_sweep_slab(const SlabPlanes &sp, int colour, const PhiloxLaunch &ph,
                                    const IsingThr &ithr, const BcTable *btab, cudaStream_t st)
 {
+    if (injected_launch_failure())
+        return cudaErrorLaunchFailure;
     const int64_t PS = (sp.rows + 2) * sp.W;
     const uint32_t yg0 = (uint32_t)sp.y0;
     if (sp.model == 0) {

@@ -78,7 +78,9 @@ struct Request {
     int64_t record_every = 0;
     int32_t keep = 0;
     double t_arrival = 0, t_admit = -1, t_done = -1;
+    double deadline = 0;           // server clock; <= 0: none
     int32_t state = ISG_REQ_QUEUED;
+    int32_t error = ISG_OK;        // the status that failed it (ISG_REQ_FAILED)
     int64_t queued_sweeps = 0;  // sweeps queued on the device so far
     bool finish_queued = false;
     bool small = false;
@@ -92,6 +94,11 @@ struct Request {
     int64_t rec_read = 0;     // periodic records already read by the caller
     cudaStream_t stream = nullptr;  // own stream (large requests)
     cudaEvent_t done = nullptr;
+    // large requests: events after their last two chunks; a chunk is queued
+    // only once the one two before it has finished, so at most two chunks
+    // are ever in flight (cancellation and deadlines act within them)
+    cudaEvent_t chunk_ev[2] = {nullptr, nullptr};
+    int64_t chunks_queued = 0;
     bool freed = true;
 };
 
@@ -178,9 +185,9 @@ isg_status admit(isg_server *s, Request &r)
         }
     }
     cudaStream_t st = req_stream(s, r);
-    cudaError_t e = cudaMallocAsync(&r.planes, isg_lattice_bytes(r.model, r.L), st);
+    cudaError_t e = dev_malloc_async(&r.planes, isg_lattice_bytes(r.model, r.L), st);
     if (e == cudaSuccess)
-        e = cudaMallocAsync(&r.recs, record_stride(r.L) * (size_t)(r.rec_cap + 1), st);
+        e = dev_malloc_async(&r.recs, record_stride(r.L) * (size_t)(r.rec_cap + 1), st);
     r.freed = false;
     s->used += r.bytes;
     if (e != cudaSuccess) {
@@ -189,6 +196,9 @@ isg_status admit(isg_server *s, Request &r)
     }
     if (!r.done)
         SCUDA(cudaEventCreate(&r.done), "request event");
+    for (int k = 0; k < 2 && !r.small; ++k)
+        if (!r.chunk_ev[k])
+            SCUDA(cudaEventCreateWithFlags(&r.chunk_ev[k], cudaEventDisableTiming), "chunk event");
     Planes pl{r.planes, r.L, r.L / 64, r.model};
     PhiloxLaunch ph0, ph1;
     philox_launch_consts(r.seed, 0u, 2u, &ph0);
@@ -216,6 +226,32 @@ isg_status queue_finish(isg_server *s, Request &r)
     return ISG_OK;
 }
 
+// Take a queued or running request out of the schedule for good: cancelled
+// by the caller, past its deadline, or failed (its allocation or a launch).
+// A running request's queued device work is waited for (its stream: at most
+// one chunk), so that nothing still reads its memory when it is freed and
+// its final-record slot is reused.
+void drop(isg_server *s, Request &r, int32_t state, int32_t error)
+{
+    auto q = std::find(s->queue.begin(), s->queue.end(), r.id);
+    if (q != s->queue.end())
+        s->queue.erase(q);
+    auto a = std::find(s->active.begin(), s->active.end(), r.id);
+    if (a != s->active.end()) {
+        s->active.erase(a);
+        cudaStreamSynchronize(req_stream(s, r));
+        cudaGetLastError();
+        release_device(s, r);
+        if (r.final_slot >= 0) {
+            s->free_final_slots.push_back(r.final_slot);
+            r.final_slot = -1;
+        }
+    }
+    r.state = state;
+    r.error = error;
+    r.t_done = clock_now(s);
+}
+
 isg_status run_round(isg_server *s)
 {
     const double now = clock_now(s);
@@ -239,27 +275,45 @@ isg_status run_round(isg_server *s)
             ++i;
         }
     }
-    // 2. admit in arrival order while slots and the memory budget allow
+    // requests past their deadline leave the schedule (queued or running)
+    std::vector<uint64_t> late;
+    for (uint64_t id : s->queue)
+        if (s->reqs[id]->deadline > 0 && now > s->reqs[id]->deadline)
+            late.push_back(id);
+    for (uint64_t id : s->active)
+        if (s->reqs[id]->deadline > 0 && now > s->reqs[id]->deadline)
+            late.push_back(id);
+    for (uint64_t id : late)
+        drop(s, *s->reqs[id], ISG_REQ_EXPIRED, ISG_OK);
+    // 2. admit in arrival order while slots and the memory budget allow; a
+    // request whose allocation fails is failed alone
     while (!s->queue.empty() && (int32_t)s->active.size() < s->max_active) {
         Request &r = *s->reqs[s->queue.front()];
         if (r.t_arrival > now || s->used + r.bytes > s->budget)
             break;
         s->queue.pop_front();
-        isg_status st = admit(s, r);
-        if (st != ISG_OK)
-            return st;
         s->active.push_back(r.id);
+        const isg_status st = admit(s, r);
+        if (st != ISG_OK)
+            drop(s, r, ISG_REQ_FAILED, st);
     }
     // 3. advance every running request by one chunk
     const int buf = (int)(s->round & 1);
     if (s->round >= 2)  // this parity's host buffers were last read by round - 2
         SCUDA(cudaEventSynchronize(s->round_done[buf]), "round sync");
     std::vector<std::pair<int64_t, int32_t>> batch;  // (work, item)
+    std::vector<uint64_t> batch_ids;                  // request of each item
+    std::vector<std::pair<uint64_t, isg_status>> failed;
     int32_t n_items = 0;
     for (uint64_t id : s->active) {
         Request &r = *s->reqs[id];
         if (r.queued_sweeps >= r.n_sweeps)
             continue;
+        if (!r.small && r.chunks_queued >= 2 &&
+            cudaEventQuery(r.chunk_ev[r.chunks_queued & 1]) != cudaSuccess) {
+            cudaGetLastError();  // not ready: two chunks still in flight
+            continue;
+        }
         const int64_t n = std::min(s->chunk, r.n_sweeps - r.queued_sweeps);
         const int64_t t0 = r.queued_sweeps;
         if (r.small) {
@@ -309,6 +363,7 @@ isg_status run_round(isg_server *s)
             it.rec_pitch = record_stride(r.L);
             it.rec_cap = (int32_t)std::max<int64_t>(r.rec_cap, 1);
             batch.emplace_back(r.L * r.L * (r.model + 1), slot);
+            batch_ids.push_back(id);
             ++n_items;
         } else {
             Planes pl{r.planes, r.L, r.L / 64, r.model};
@@ -325,18 +380,26 @@ isg_status run_round(isg_server *s)
                         bc_table(b, r.delta, &tab);
                     last = b;
                 }
-                for (int c = 0; c < 2; ++c) {
+                cudaError_t e = cudaSuccess;
+                for (int c = 0; c < 2 && e == cudaSuccess; ++c) {
                     PhiloxLaunch ph;
                     philox_launch_consts(r.seed, (uint32_t)t, (uint32_t)c, &ph);
-                    SCUDA(launch_half_sweep(pl, c, ph, ithr, r.model == ISG_ISING ? nullptr : &tab,
-                                            r.stream), "half-sweep launch");
+                    e = launch_half_sweep(pl, c, ph, ithr, r.model == ISG_ISING ? nullptr : &tab,
+                                          r.stream);
                 }
-                if (r.record_every > 0 && (t + 1) % r.record_every == 0) {
+                if (e == cudaSuccess && r.record_every > 0 && (t + 1) % r.record_every == 0) {
                     uint8_t *rec = r.recs + record_stride(r.L) * (size_t)((t + 1) / r.record_every - 1);
-                    SCUDA(cudaMemsetAsync(rec, 0, record_stride(r.L), r.stream), "record clear");
-                    SCUDA(launch_measure(pl, rec, t + 1, r.stream), "measure launch");
+                    e = cudaMemsetAsync(rec, 0, record_stride(r.L), r.stream);
+                    if (e == cudaSuccess)
+                        e = launch_measure(pl, rec, t + 1, r.stream);
+                }
+                if (e != cudaSuccess) {
+                    failed.push_back({id, scuda(e, "request launch")});
+                    break;
                 }
             }
+            cudaEventRecord(r.chunk_ev[r.chunks_queued & 1], r.stream);
+            r.chunks_queued += 1;
         }
         r.queued_sweeps += n;
     }
@@ -360,9 +423,19 @@ isg_status run_round(isg_server *s)
         SCUDA(cudaMemcpyAsync(s->d_args[buf], s->h_args[buf], sizeof(EnsArgs),
                               cudaMemcpyHostToDevice, s->stream), "args");
         SCUDA(cudaMemsetAsync(s->d_counter + buf, 0, sizeof(int32_t), s->stream), "counter");
-        k_ensemble<<<s->blocks, s->threads, (size_t)kSmemLimit, s->stream>>>(s->d_args[buf]);
-        SCUDA(cudaGetLastError(), "batch launch");
+        cudaError_t e = cudaErrorLaunchFailure;
+        if (!injected_launch_failure()) {
+            k_ensemble<<<s->blocks, s->threads, (size_t)kSmemLimit, s->stream>>>(s->d_args[buf]);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {  // every request of this batch fails
+            const isg_status st = scuda(e, "batch launch");
+            for (uint64_t id : batch_ids)
+                failed.push_back({id, st});
+        }
     }
+    for (const auto &f : failed)
+        drop(s, *s->reqs[f.first], ISG_REQ_FAILED, f.second);
     // queue the finish of requests whose last chunk went out
     for (uint64_t id : s->active) {
         Request &r = *s->reqs[id];
@@ -413,19 +486,19 @@ isg_status isg_server_create(const isg_server_desc *d, isg_server **out)
     }
     const size_t na = (size_t)s->max_active;
     const size_t nt = na * (size_t)s->chunk;
-    cudaError_t e = cudaMalloc(&s->d_counter, sizeof(int32_t) * 2);
+    cudaError_t e = dev_malloc(&s->d_counter, sizeof(int32_t) * 2);
     if (e == cudaSuccess)
         e = cudaMallocHost(&s->h_finals, sizeof(int64_t) * 4 * na);
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
-        e = cudaMalloc(&s->d_items[k], sizeof(EnsItem) * na);
+        e = dev_malloc(&s->d_items[k], sizeof(EnsItem) * na);
         if (e == cudaSuccess) e = cudaMallocHost(&s->h_items[k], sizeof(EnsItem) * na);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_order[k], sizeof(int32_t) * na);
+        if (e == cudaSuccess) e = dev_malloc(&s->d_order[k], sizeof(int32_t) * na);
         if (e == cudaSuccess) e = cudaMallocHost(&s->h_order[k], sizeof(int32_t) * na);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_args[k], sizeof(EnsArgs));
+        if (e == cudaSuccess) e = dev_malloc(&s->d_args[k], sizeof(EnsArgs));
         if (e == cudaSuccess) e = cudaMallocHost(&s->h_args[k], sizeof(EnsArgs));
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_ithr[k], sizeof(IsingThr) * nt);
+        if (e == cudaSuccess) e = dev_malloc(&s->d_ithr[k], sizeof(IsingThr) * nt);
         if (e == cudaSuccess) e = cudaMallocHost(&s->h_ithr[k], sizeof(IsingThr) * nt);
-        if (e == cudaSuccess) e = cudaMalloc(&s->d_btab[k], sizeof(BcTable) * nt);
+        if (e == cudaSuccess) e = dev_malloc(&s->d_btab[k], sizeof(BcTable) * nt);
         if (e == cudaSuccess) e = cudaMallocHost(&s->h_btab[k], sizeof(BcTable) * nt);
         if (e == cudaSuccess) e = cudaEventCreate(&s->round_done[k]);
     }
@@ -459,6 +532,8 @@ void isg_server_destroy(isg_server *s)
         Request &r = *kv.second;
         release_device(s, r);
         if (r.done) cudaEventDestroy(r.done);
+        for (cudaEvent_t ev : r.chunk_ev)
+            if (ev) cudaEventDestroy(ev);
     }
     cudaDeviceSynchronize();
     for (cudaStream_t st : s->free_streams)
@@ -491,9 +566,9 @@ isg_status isg_server_submit(isg_server *s, const isg_request *q, uint64_t *id)
         *id = 0;
     if (!s || !q || !id)
         return sfail(ISG_ERR_INVALID, "bad arguments");
-    if (isg_lattice_bytes(q->model, q->L) == 0 || q->L % 256 != 0)
-        return sfail(ISG_ERR_INVALID, "request L %lld: must be a valid lattice side and a "
-                     "multiple of 256", (long long)q->L);
+    if (isg_lattice_bytes(q->model, q->L) == 0)
+        return sfail(ISG_ERR_INVALID, "request L %lld: must be a valid lattice side (a multiple "
+                     "of 64)", (long long)q->L);
     if (q->n_sweeps < 1 || q->n_sweeps > (int64_t)0xFFFFFFFFLL || q->record_every < 0)
         return sfail(ISG_ERR_INVALID, "bad n_sweeps or record_every");
     if (q->n_pieces < 1 || !q->t_start || !q->beta || q->t_start[0] != 0)
@@ -518,6 +593,7 @@ isg_status isg_server_submit(isg_server *s, const isg_request *q, uint64_t *id)
     r->record_every = q->record_every;
     r->keep = q->keep_result;
     r->t_arrival = q->arrival_time >= 0 ? q->arrival_time : clock_now(s);
+    r->deadline = q->deadline > 0 ? q->deadline : 0;
     r->small = smem_bytes_for(r->model, r->L) <= (size_t)kSmemLimit;
     r->rec_cap = q->record_every > 0 ? q->n_sweeps / q->record_every : 0;
     // batched requests record inside the kernel at multiples of record_every
@@ -590,6 +666,22 @@ isg_status isg_server_poll(isg_server *s, uint64_t id, isg_result *out)
     out->t_admit = r.t_admit;
     out->t_done = r.t_done;
     out->records = r.state == ISG_REQ_DONE ? r.rec_cap - r.rec_read : 0;
+    out->error = r.error;
+    return ISG_OK;
+}
+
+isg_status isg_server_cancel(isg_server *s, uint64_t id)
+{
+    if (!s)
+        return sfail(ISG_ERR_INVALID, "server is NULL");
+    auto it = s->reqs.find(id);
+    if (it == s->reqs.end())
+        return sfail(ISG_ERR_INVALID, "unknown request %llu", (unsigned long long)id);
+    Request &r = *it->second;
+    if (r.state != ISG_REQ_QUEUED && r.state != ISG_REQ_RUNNING)
+        return sfail(ISG_ERR_INVALID, "request %llu has already left the schedule (state %d)",
+                     (unsigned long long)id, r.state);
+    drop(s, r, ISG_REQ_CANCELLED, ISG_OK);
     return ISG_OK;
 }
 
@@ -642,7 +734,7 @@ isg_status isg_server_get_lattice(isg_server *s, uint64_t id, int8_t *out)
     Planes pl{r.planes, r.L, r.L / 64, r.model};
     const size_t n = (size_t)r.L * (size_t)r.L;
     int8_t *d = nullptr;
-    SCUDA(cudaMalloc(&d, n), "staging allocation");
+    SCUDA(dev_malloc(&d, n), "staging allocation");
     cudaError_t e = launch_unpack_rect(pl, 0, 0, r.L, r.L, d, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, d, n, cudaMemcpyDeviceToHost, s->stream);

@@ -150,11 +150,11 @@ isg_status isg_slab_create(const isg_slab_desc *d, isg_slab **out)
     s->seed = d->seed;
     s->delta = d->model == ISG_BLUME_CAPEL ? d->delta : 0.0;
     s->stream = (cudaStream_t)d->stream;
-    cudaError_t e = cudaMalloc(&s->planes, 4 * plane_words(s) * nplanes(s->model));
+    cudaError_t e = dev_malloc(&s->planes, 4 * plane_words(s) * nplanes(s->model));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->record, record_bytes(s));
+        e = dev_malloc(&s->record, record_bytes(s));
     if (e == cudaSuccess)
-        e = cudaMalloc(&s->d_flag, sizeof(int32_t));
+        e = dev_malloc(&s->d_flag, sizeof(int32_t));
     // halo rows start as zero words until the first isg_slab_set_halos
     if (e == cudaSuccess)
         e = cudaMemsetAsync(s->planes, 0, 4 * plane_words(s) * nplanes(s->model), s->stream);
@@ -201,7 +201,7 @@ isg_status isg_slab_set(isg_slab *s, const int8_t *host, int64_t t)
         return report_error(ISG_ERR_INVALID, "sweep index %lld out of range", (long long)t);
     const size_t n = (size_t)s->rows * (size_t)s->L;
     int8_t *d = nullptr;
-    SLAB_CUDA(cudaMallocAsync(&d, n, s->stream), "staging allocation");
+    SLAB_CUDA(dev_malloc_async(&d, n, s->stream), "staging allocation");
     int32_t bad = 0;
     cudaError_t e = cudaMemcpyAsync(d, host, n, cudaMemcpyHostToDevice, s->stream);
     if (e == cudaSuccess)
@@ -227,7 +227,7 @@ isg_status isg_slab_get(isg_slab *s, int8_t *out)
         return report_error(ISG_ERR_INVALID, "slab and out must not be NULL");
     const size_t n = (size_t)s->rows * (size_t)s->L;
     int8_t *d = nullptr;
-    SLAB_CUDA(cudaMallocAsync(&d, n, s->stream), "staging allocation");
+    SLAB_CUDA(dev_malloc_async(&d, n, s->stream), "staging allocation");
     cudaError_t e = launch_slab_convert(planes_of(s), d, 0, nullptr, s->stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, d, n, cudaMemcpyDeviceToHost, s->stream);

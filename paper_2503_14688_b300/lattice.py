@@ -257,3 +257,10 @@ def xi_integral(r, c, r_cut: float) -> float:
     c = np.ascontiguousarray(np.asarray(c, dtype=np.float64))
     return float(lib().isg_xi_integral(r.size, r.ctypes.data_as(_abi._F64P),
                                        c.ctypes.data_as(_abi._F64P), float(r_cut)))
+
+
+def inject_fault(what: int, after: int):
+    """isg_debug_inject: the after-th device allocation (what =
+    ISG_INJECT_ALLOC) or sweep launch (ISG_INJECT_LAUNCH) from now on fails,
+    once; after = 0 disarms.  For testing error paths on the host."""
+    check(lib().isg_debug_inject(int(what), int(after)))

@@ -21,6 +21,7 @@ class Result:
     t_admit: float
     t_done: float
     records: int
+    error: int = 0
 
 
 class Server:
@@ -49,13 +50,13 @@ class Server:
 
     def submit(self, model: int, L: int, seed: int, n_sweeps: int, t_start, beta,
                delta: float = 0.0, record_every: int = 0, keep: bool = False,
-               arrival_time: float = -1.0) -> int:
+               arrival_time: float = -1.0, deadline: float = 0.0) -> int:
         ts = np.ascontiguousarray(np.asarray(t_start, dtype=np.int64))
         bs = np.ascontiguousarray(np.asarray(beta, dtype=np.float64))
         q = _abi.isg_request(int(model), int(L), int(seed) & (2**64 - 1), float(delta),
                              int(n_sweeps), ts.size, ts.ctypes.data_as(_abi._I64P),
                              bs.ctypes.data_as(_abi._F64P), int(record_every), int(bool(keep)),
-                             float(arrival_time))
+                             float(arrival_time), float(deadline))
         rid = ctypes.c_uint64()
         check(self._lib.isg_server_submit(self._h, ctypes.byref(q), ctypes.byref(rid)))
         self.L[rid.value] = int(L)
@@ -73,7 +74,10 @@ class Server:
         r = _abi.isg_result()
         check(self._lib.isg_server_poll(self._h, rid, ctypes.byref(r)))
         return Result(r.state, r.sweeps_done, r.B, r.M, r.Q, r.t_arrival, r.t_admit, r.t_done,
-                      r.records)
+                      r.records, r.error)
+
+    def cancel(self, rid: int):
+        check(self._lib.isg_server_cancel(self._h, rid))
 
     def read_records(self, rid: int) -> List[Obs]:
         n = self.poll(rid).records

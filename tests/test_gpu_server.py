@@ -42,8 +42,10 @@ def test_results_same_alone_and_in_the_mix(isg):
     srv = isg.Server(hbm_budget=8 << 30, max_active=6, chunk_sweeps=chunk)
     rng = np.random.default_rng(5)
     reqs = []
-    specs = [(0, 256), (1, 256), (0, 512), (0, 1024), (1, 512), (0, 2048), (1, 1024), (0, 256),
-             (1, 768), (0, 1280), (0, 512), (1, 256)]
+    # every valid side, not only powers of two: 64, 192, 320 arrive while
+    # others (shared-memory batch and own-stream lattices) run
+    specs = [(0, 256), (1, 256), (0, 512), (0, 1024), (1, 512), (0, 2048), (1, 1024), (0, 64),
+             (1, 192), (0, 320), (1, 768), (0, 1280), (0, 512), (1, 320), (0, 192), (1, 64)]
     for i, (model, L) in enumerate(specs):
         Tc = wl.T_C_ISING if model == 0 else wl.T_C_BLUME_CAPEL
         n = int(rng.integers(30, 90))
@@ -98,7 +100,7 @@ def test_admission_respects_budget(isg):
 def test_server_rejects_bad_requests(isg):
     srv = isg.Server(hbm_budget=1 << 30, max_active=2, chunk_sweeps=10)
     with pytest.raises(isg.IsgError):
-        srv.submit(0, 320, 1, 10, [0], [0.4])          # not a multiple of 256
+        srv.submit(0, 100, 1, 10, [0], [0.4])          # not a multiple of 64
     with pytest.raises(isg.IsgError):
         srv.submit(0, 256, 1, 10, [5], [0.4])          # schedule must start at 0
     with pytest.raises(isg.IsgError):
