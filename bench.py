@@ -183,7 +183,7 @@ def batched_bench(sweeps=10000, n_rep=4096, record_every=1000):
     stream = torch.cuda.Stream()
     ens = P.Ensemble(Ls, seeds, stream=stream, record_capacity=sweeps // record_every + 1)
     ens.init_random()
-    threads = ens.autotune(4)
+    tune, cands = ens.autotune(50, with_candidates=True)
     ens.sweep(4, beta=wl.BETA_C_ISING)  # warm-up (graph instantiation)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -226,7 +226,12 @@ def batched_bench(sweeps=10000, n_rep=4096, record_every=1000):
     return {"workload": f"{n_rep} Ising replicas, L uniform in {{64..1024}}, beta_c, "
                         f"{sweeps} sweeps in one persistent launch, records every {record_every}",
             "value": batched, "unit": UNIT, "ms": ms, "spins": spins, "record_rows": len(rows),
-            "threads_per_cta": threads,
+            "tuning": tune,
+            "tuning_candidates": [[c["threads_per_cta"], c["half_teams"], c["sweeps_per_launch"],
+                                   c["multi_words"], c["multi_band"], round(c["ms"], 3)]
+                                  for c in cands],
+            "tuning_candidates_fields": "threads_per_cta, half_teams, sweeps_per_launch, "
+                                        "multi_words, multi_band, ms over 50 sweeps",
             "single_lattice_equal_spins": {"L": Ls1, "value": single, "unit": UNIT},
             "ratio_vs_single": batched / single,
             "one_lattice_at_a_time": {"sweeps": sweeps_alone, "value": one_at_a_time,

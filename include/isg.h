@@ -294,10 +294,39 @@ isg_status isg_ensemble_get(isg_ensemble *ens, int64_t r, int8_t *out);
 isg_status isg_ensemble_info(const isg_ensemble *ens, int64_t *n, int64_t *sweep,
                              int64_t *pending, int32_t *threads_per_cta);
 
-/* Pick the CTA size of the persistent kernel (256, 512 or 1024 threads) by
- * timing `sweeps` sweeps of each on a copy of the replicas (their state is
- * not changed).  *threads_out (may be NULL) = the choice.  Synchronises. */
-isg_status isg_ensemble_autotune(isg_ensemble *ens, int64_t sweeps, int32_t *threads_out);
+/* Launch shape of an ensemble's sweeps.  Part 0, the persistent
+ * shared-memory kernel: threads per CTA (256, 512, 1024), whether replicas
+ * that fit half the shared memory run on half-CTA teams, and how many sweeps
+ * one launch covers (0: the whole call; else a call is cut into launches of
+ * that many sweeps, rounded up to a multiple of record_every, at most 32).
+ * Part 1, the multi-lattice launches of the replicas too large for shared
+ * memory: words per thread (1, 2, 4) and rows per thread band (16, 32, 64);
+ * 0 = chosen from L.  The results never depend on the shape. */
+typedef struct {
+    int32_t threads_per_cta;
+    int32_t half_teams;
+    int64_t sweeps_per_launch;
+    int32_t multi_words;
+    int32_t multi_band;
+    double ms;     /* isg_ensemble_autotune: this candidate's time for its part */
+    int32_t part;  /* isg_ensemble_autotune: 0 persistent kernel, 1 multi-lattice */
+} isg_ensemble_tuning;
+
+/* Choose the launch shape by timing `sweeps` sweeps (50 or more recommended)
+ * of every candidate on a copy of the replicas (their state is not changed):
+ * part 0 over 3 CTA sizes x teams on/off x {whole call, sweeps/5 per
+ * launch}, part 1 over words {auto, 1, 2, 4} x bands {auto, 16, 32, 64}; the
+ * fastest of each part is kept.  *best (may be NULL) = the choice, its ms the
+ * sum of both parts' times; tried[0..min(max_tried, n))] (may be NULL when
+ * max_tried is 0) = every candidate with its time, *n_tried = their number.
+ * Synchronises. */
+isg_status isg_ensemble_autotune(isg_ensemble *ens, int64_t sweeps, isg_ensemble_tuning *best,
+                                 isg_ensemble_tuning *tried, int64_t max_tried, int64_t *n_tried);
+
+/* Set or read the launch shape (ms and part ignored / 0).  ISG_ERR_INVALID
+ * for a shape outside the ranges above.  Set synchronises. */
+isg_status isg_ensemble_set_tuning(isg_ensemble *ens, const isg_ensemble_tuning *t);
+isg_status isg_ensemble_get_tuning(const isg_ensemble *ens, isg_ensemble_tuning *t);
 
 /* ---------------------------------------------------------------------------
  * Request server with continuous batching.  Each request is one lattice

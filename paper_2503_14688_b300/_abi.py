@@ -49,6 +49,12 @@ class isg_ensemble_desc(ctypes.Structure):
                 ("record_capacity", ctypes.c_int64)]
 
 
+class isg_ensemble_tuning(ctypes.Structure):
+    _fields_ = [("threads_per_cta", ctypes.c_int32), ("half_teams", ctypes.c_int32),
+                ("sweeps_per_launch", ctypes.c_int64), ("multi_words", ctypes.c_int32),
+                ("multi_band", ctypes.c_int32), ("ms", ctypes.c_double), ("part", ctypes.c_int32)]
+
+
 class isg_server_desc(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_size_t), ("max_active", ctypes.c_int32),
                 ("chunk_sweeps", ctypes.c_int64), ("stream", ctypes.c_void_p)]
@@ -126,7 +132,10 @@ PROTOTYPES = {
     "isg_ensemble_read_records": (_I32, [_P, _I64, ctypes.POINTER(isg_obs), _I64P]),
     "isg_ensemble_get": (_I32, [_P, _I64, _I8P]),
     "isg_ensemble_info": (_I32, [_P, _I64P, _I64P, _I64P, _I32P]),
-    "isg_ensemble_autotune": (_I32, [_P, _I64, _I32P]),
+    "isg_ensemble_autotune": (_I32, [_P, _I64, ctypes.POINTER(isg_ensemble_tuning),
+                                     ctypes.POINTER(isg_ensemble_tuning), _I64, _I64P]),
+    "isg_ensemble_set_tuning": (_I32, [_P, ctypes.POINTER(isg_ensemble_tuning)]),
+    "isg_ensemble_get_tuning": (_I32, [_P, ctypes.POINTER(isg_ensemble_tuning)]),
     "isg_server_create": (_I32, [ctypes.POINTER(isg_server_desc), ctypes.POINTER(_P)]),
     "isg_server_destroy": (None, [_P]),
     "isg_server_submit": (_I32, [_P, ctypes.POINTER(isg_request), _U64P]),

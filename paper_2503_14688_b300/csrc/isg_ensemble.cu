@@ -90,9 +90,18 @@ struct isg_ensemble {
         std::vector<int64_t> reps;  // replica indices
     };
     std::vector<GlobalGroup> groups;
+    // per-launch arguments and work counters of the persistent launches of
+    // one call (sweeps_per_launch > 0 cuts a call into several)
     int32_t *d_counter = nullptr;
     EnsArgs *d_args = nullptr;
     EnsArgs *h_args = nullptr;  // pinned
+    // launch shape (isg_ensemble_autotune, isg_ensemble_set_tuning)
+    bool teams = true;                 // half-CTA teams once replicas fit half the memory
+    int32_t split_from_teams = 0;      // split point with teams (n_smem: no team-sized replica)
+    uint32_t half_words_teams = 0;
+    size_t smem_whole = 0, smem_teams = 0;
+    int64_t sweeps_per_launch = 0;     // 0: one persistent launch per call
+    int32_t multi_V = 0, multi_H = 0;  // multi-lattice words per thread, band rows; 0 = automatic
     IsingThr *d_ithr = nullptr, *h_ithr = nullptr;
     BcTable *d_btab = nullptr, *h_btab = nullptr;
     int64_t thr_cap = 0;
@@ -114,6 +123,12 @@ namespace {
 // launches carry 24 KB of parameters each, so fewer of them.
 constexpr int64_t kMaxGraphLaunches = (int64_t)1 << 16;
 constexpr int64_t kMaxGraphMultiLaunches = 2048;
+// Most persistent launches one call is cut into.
+constexpr int kMaxLaunches = 32;
+
+// Shared memory, split point and grid of the persistent kernel for the
+// current shape (threads per CTA, teams on or off).
+isg_status apply_shape(isg_ensemble *e);
 
 void free_tables(isg_ensemble *e)
 {
@@ -166,33 +181,51 @@ int occupancy_blocks(int threads, size_t smem)
 
 // Queue one launch of the shared-memory kernel over all its replicas plus
 // the global-memory sweeps of the large replicas, for sweeps t .. t+n-1.
+// Persistent launches of one call, sweeps t .. t+n-1: sweeps_per_launch (0 =
+// all of them) per launch, rounded up to a multiple of record_every so that
+// every launch's records fall on the call's record rows.
+int64_t launch_sweeps(const isg_ensemble *e, int64_t n, int64_t record_every)
+{
+    int64_t k = e->sweeps_per_launch > 0 ? std::min(e->sweeps_per_launch, n) : n;
+    if ((n + k - 1) / k > kMaxLaunches)
+        k = (n + kMaxLaunches - 1) / kMaxLaunches;
+    if (record_every > 0)
+        k = (k + record_every - 1) / record_every * record_every;
+    return std::max<int64_t>(k, 1);
+}
+
 isg_status queue_sweeps(isg_ensemble *e, int64_t n, int64_t record_every, int64_t rec_row0)
 {
     cudaStream_t st = e->stream;
     if (e->n_smem > 0 && n > 0) {
-        EnsArgs &a = *e->h_args;
-        a.items = e->d_items;
-        a.order = e->d_order;
-        a.n_order = e->n_smem;
-        a.counter = e->d_counter;
-        a.ithr = e->d_ithr;
-        a.btab = e->d_btab;
-        a.rec_ring = e->rec_ring;
-        a.row_bytes = e->row_bytes;
-        a.rec_cap = (int32_t)e->rec_cap;
-        a.rec_row0 = (int32_t)rec_row0;
-        a.t0 = (uint32_t)e->t;
-        a.nsweeps = (int32_t)n;
-        a.record_every = (int32_t)record_every;
-        a.half_words = e->half_words;
-        a.split_from = e->split_from;
-        ECUDA(cudaMemcpyAsync(e->d_args, e->h_args, sizeof(EnsArgs), cudaMemcpyHostToDevice, st),
-              "ensemble args");
-        ECUDA(cudaMemsetAsync(e->d_counter, 0, sizeof(int32_t), st), "work counter");
-        if (injected_launch_failure())
-            return ecuda(cudaErrorLaunchFailure, "ensemble launch");
-        k_ensemble<<<e->blocks, e->threads, e->smem, st>>>(e->d_args);
-        ECUDA(cudaGetLastError(), "ensemble launch");
+        const int64_t k = launch_sweeps(e, n, record_every);
+        int ci = 0;
+        for (int64_t c0 = 0; c0 < n; c0 += k, ++ci) {
+            EnsArgs &a = e->h_args[ci];
+            a.items = e->d_items;
+            a.order = e->d_order;
+            a.n_order = e->n_smem;
+            a.counter = e->d_counter + ci;
+            a.ithr = e->d_ithr + c0;
+            a.btab = e->d_btab ? e->d_btab + c0 : nullptr;
+            a.rec_ring = e->rec_ring;
+            a.row_bytes = e->row_bytes;
+            a.rec_cap = (int32_t)e->rec_cap;
+            a.rec_row0 = record_every > 0 ? (int32_t)((rec_row0 + c0 / record_every) % e->rec_cap)
+                                          : (int32_t)rec_row0;
+            a.t0 = (uint32_t)(e->t + c0);
+            a.nsweeps = (int32_t)std::min(k, n - c0);
+            a.record_every = (int32_t)record_every;
+            a.half_words = e->half_words;
+            a.split_from = e->split_from;
+            ECUDA(cudaMemcpyAsync(e->d_args + ci, &a, sizeof(EnsArgs), cudaMemcpyHostToDevice, st),
+                  "ensemble args");
+            ECUDA(cudaMemsetAsync(e->d_counter + ci, 0, sizeof(int32_t), st), "work counter");
+            if (injected_launch_failure())
+                return ecuda(cudaErrorLaunchFailure, "ensemble launch");
+            k_ensemble<<<e->blocks, e->threads, e->smem, st>>>(e->d_args + ci);
+            ECUDA(cudaGetLastError(), "ensemble launch");
+        }
     }
     for (int64_t i = 0; i < n && !e->groups.empty(); ++i) {
         const uint32_t t = (uint32_t)(e->t + i);
@@ -200,7 +233,8 @@ isg_status queue_sweeps(isg_ensemble *e, int64_t n, int64_t record_every, int64_
             for (const auto &gr : e->groups)
                 ECUDA(launch_half_sweep_multi(gr.model, gr.L, gr.planes.data(), gr.seeds.data(),
                                               (int)gr.planes.size(), t, c, e->h_ithr[i],
-                                              e->h_btab ? &e->h_btab[i] : nullptr, st),
+                                              e->h_btab ? &e->h_btab[i] : nullptr, st, e->multi_V,
+                                              e->multi_H),
                       "half-sweep launch");
         if (record_every > 0 && (i + 1) % record_every == 0) {
             const int64_t row = (rec_row0 + (i + 1) / record_every - 1) % e->rec_cap;
@@ -213,6 +247,23 @@ isg_status queue_sweeps(isg_ensemble *e, int64_t n, int64_t record_every, int64_
                       "measure launch");
             }
         }
+    }
+    return ISG_OK;
+}
+
+isg_status apply_shape(isg_ensemble *e)
+{
+    const bool teams = e->teams && e->split_from_teams < e->n_smem;
+    e->split_from = teams ? e->split_from_teams : e->n_smem;
+    e->half_words = teams ? e->half_words_teams : 0;
+    e->smem = teams ? e->smem_teams : e->smem_whole;
+    if (e->n_smem > 0 && e->smem > 48 * 1024)
+        ECUDA(cudaFuncSetAttribute(k_ensemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e->smem),
+              "shared memory opt-in");
+    e->blocks = occupancy_blocks(e->threads, e->smem);
+    if (e->exec) {  // the launch shape changed: rebuild the graph next time
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
     }
     return ISG_OK;
 }
@@ -279,11 +330,11 @@ isg_status isg_ensemble_create(const isg_ensemble_desc *d, isg_ensemble **out)
     if (err == cudaSuccess)
         err = dev_malloc(&e->rec_ring, e->row_bytes * (uint64_t)e->rec_cap);
     if (err == cudaSuccess)
-        err = dev_malloc(&e->d_counter, sizeof(int32_t));
+        err = dev_malloc(&e->d_counter, sizeof(int32_t) * kMaxLaunches);
     if (err == cudaSuccess)
-        err = dev_malloc(&e->d_args, sizeof(EnsArgs));
+        err = dev_malloc(&e->d_args, sizeof(EnsArgs) * kMaxLaunches);
     if (err == cudaSuccess)
-        err = cudaMallocHost(&e->h_args, sizeof(EnsArgs));
+        err = cudaMallocHost(&e->h_args, sizeof(EnsArgs) * kMaxLaunches);
     if (err != cudaSuccess)
         return cleanup(ecuda(err, "ensemble allocation"));
     // work split: shared-memory replicas largest first; the rest global
@@ -319,17 +370,19 @@ isg_status isg_ensemble_create(const isg_ensemble_desc *d, isg_ensemble **out)
     // lattices that fit half the largest shared-memory request run on
     // half-CTA teams (isg_batch.cuh); the request covers two of them
     const size_t half_cap = ((size_t)kBatchSmemMax / 2) & ~(size_t)15;
-    e->split_from = e->n_smem;
+    e->smem_whole = smem;
+    e->split_from_teams = e->n_smem;
     for (int32_t i = 0; i < e->n_smem; ++i)
         if (smem_bytes_for(e->model[order[i]], e->L[order[i]]) <= half_cap) {
-            e->split_from = i;
+            e->split_from_teams = i;
             break;
         }
-    if (e->split_from < e->n_smem) {
-        const size_t half_bytes =
-            (smem_bytes_for(e->model[order[e->split_from]], e->L[order[e->split_from]]) + 15) & ~(size_t)15;
-        e->half_words = (uint32_t)(half_bytes / 4);
-        smem = std::max(smem, 2 * half_bytes);
+    e->smem_teams = smem;
+    if (e->split_from_teams < e->n_smem) {
+        const size_t half_bytes = (smem_bytes_for(e->model[order[e->split_from_teams]],
+                                                  e->L[order[e->split_from_teams]]) + 15) & ~(size_t)15;
+        e->half_words_teams = (uint32_t)(half_bytes / 4);
+        e->smem_teams = std::max(smem, 2 * half_bytes);
     }
     std::vector<EnsItem> items(d->n);
     for (int64_t r = 0; r < d->n; ++r) {
@@ -350,14 +403,11 @@ isg_status isg_ensemble_create(const isg_ensemble_desc *d, isg_ensemble **out)
                          cudaMemcpyHostToDevice);
     if (err != cudaSuccess)
         return cleanup(ecuda(err, "ensemble tables"));
-    e->smem = smem;
-    if (smem > 48 * 1024) {
-        err = cudaFuncSetAttribute(k_ensemble, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess)
-            return cleanup(ecuda(err, "shared memory opt-in"));
-    }
     e->threads = 1024;
-    e->blocks = occupancy_blocks(e->threads, e->smem);
+    e->teams = e->split_from_teams < e->n_smem;
+    const isg_status ss = apply_shape(e);
+    if (ss != ISG_OK)
+        return cleanup(ss);
     *out = e;
     return ISG_OK;
 }
@@ -566,17 +616,46 @@ isg_status isg_ensemble_get(isg_ensemble *e, int64_t r, int8_t *out)
     return ISG_OK;
 }
 
-isg_status isg_ensemble_autotune(isg_ensemble *e, int64_t sweeps, int32_t *threads_out)
+isg_status isg_ensemble_get_tuning(const isg_ensemble *e, isg_ensemble_tuning *t)
 {
-    if (!e || sweeps < 1)
+    if (!e || !t)
         return efail(ISG_ERR_INVALID, "bad arguments");
-    if (e->n_smem == 0) {
-        if (threads_out)
-            *threads_out = e->threads;
-        return ISG_OK;
-    }
-    // time the shared-memory kernel on a copy of the planes, so that the
-    // ensemble's own state does not move
+    *t = isg_ensemble_tuning{};
+    t->threads_per_cta = e->threads;
+    t->half_teams = e->teams && e->split_from_teams < e->n_smem ? 1 : 0;
+    t->sweeps_per_launch = e->sweeps_per_launch;
+    t->multi_words = e->multi_V;
+    t->multi_band = e->multi_H;
+    return ISG_OK;
+}
+
+isg_status isg_ensemble_set_tuning(isg_ensemble *e, const isg_ensemble_tuning *t)
+{
+    if (!e || !t)
+        return efail(ISG_ERR_INVALID, "bad arguments");
+    if (t->threads_per_cta != 256 && t->threads_per_cta != 512 && t->threads_per_cta != 1024)
+        return efail(ISG_ERR_INVALID, "threads_per_cta must be 256, 512 or 1024");
+    if (t->sweeps_per_launch < 0 || t->multi_words < 0 || t->multi_words > 4 || t->multi_band < 0 ||
+        t->multi_band > 64)
+        return efail(ISG_ERR_INVALID, "bad launch shape");
+    ECUDA(cudaStreamSynchronize(e->stream), "stream sync");
+    e->threads = t->threads_per_cta;
+    e->teams = t->half_teams != 0;
+    e->sweeps_per_launch = t->sweeps_per_launch;
+    e->multi_V = t->multi_words;
+    e->multi_H = t->multi_band;
+    return apply_shape(e);
+}
+
+isg_status isg_ensemble_autotune(isg_ensemble *e, int64_t sweeps, isg_ensemble_tuning *best,
+                                 isg_ensemble_tuning *tried, int64_t max_tried, int64_t *n_tried)
+{
+    if (n_tried)
+        *n_tried = 0;
+    if (!e || sweeps < 1 || sweeps > INT32_MAX || max_tried < 0 || (max_tried > 0 && !tried))
+        return efail(ISG_ERR_INVALID, "bad arguments");
+    // time the candidates on a copy of the planes, so that the ensemble's
+    // own state does not move
     isg_status s = ensure_tables(e, sweeps);
     if (s != ISG_OK)
         return s;
@@ -606,63 +685,174 @@ isg_status isg_ensemble_autotune(isg_ensemble *e, int64_t sweeps, int32_t *threa
         err = cudaMemcpy(e->d_ithr, e->h_ithr, sizeof(IsingThr) * sweeps, cudaMemcpyHostToDevice);
     if (err == cudaSuccess && e->h_btab)
         err = cudaMemcpy(e->d_btab, e->h_btab, sizeof(BcTable) * sweeps, cudaMemcpyHostToDevice);
-    int best = e->threads;
-    float best_ms = 1e30f;
-    cudaEvent_t a = nullptr, b = nullptr;
+    cudaEvent_t ea = nullptr, eb = nullptr;
     if (err == cudaSuccess)
-        err = cudaEventCreate(&a);
+        err = cudaEventCreate(&ea);
     if (err == cudaSuccess)
-        err = cudaEventCreate(&b);
-    const int candidates[3] = {256, 512, 1024};
-    for (int ci = 0; ci < 3 && err == cudaSuccess; ++ci) {
-        const int nt = candidates[ci];
-        EnsArgs args{};
-        args.items = items;
-        args.order = e->d_order;
-        args.n_order = e->n_smem;
-        args.counter = e->d_counter;
-        args.ithr = e->d_ithr;
-        args.btab = e->d_btab;
-        args.rec_ring = e->rec_ring;
-        args.row_bytes = e->row_bytes;
-        args.rec_cap = (int32_t)e->rec_cap;
-        args.t0 = 0;
-        args.nsweeps = (int32_t)sweeps;
-        args.record_every = 0;
-        args.half_words = e->half_words;
-        args.split_from = e->split_from;
-        *e->h_args = args;
-        err = cudaMemcpy(e->d_args, e->h_args, sizeof(EnsArgs), cudaMemcpyHostToDevice);
-        const int blocks = occupancy_blocks(nt, e->smem);
-        for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {  // first run warms up
-            cudaMemsetAsync(e->d_counter, 0, sizeof(int32_t), e->stream);
-            cudaEventRecord(a, e->stream);
-            k_ensemble<<<blocks, nt, e->smem, e->stream>>>(e->d_args);
-            cudaEventRecord(b, e->stream);
-            err = cudaEventSynchronize(b);
-            float ms = 0;
-            if (err == cudaSuccess)
-                err = cudaEventElapsedTime(&ms, a, b);
-            if (err == cudaSuccess && rep == 1 && ms < best_ms) {
-                best_ms = ms;
-                best = nt;
-            }
-        }
+        err = cudaEventCreate(&eb);
+    // the large replicas' plane pointers inside the copy
+    std::vector<std::vector<uint32_t *>> gplanes;
+    for (const auto &gr : e->groups) {
+        gplanes.emplace_back();
+        for (int64_t r : gr.reps)
+            gplanes.back().push_back(reinterpret_cast<uint32_t *>(copy + e->plane_off[r]));
     }
-    if (a) cudaEventDestroy(a);
-    if (b) cudaEventDestroy(b);
+    const int saved_threads = e->threads;
+    const bool saved_teams = e->teams;
+    const int64_t saved_spl = e->sweeps_per_launch;
+    // time one configuration: the queued work `body`, after one warm-up run
+    auto timed = [&](auto body, double *ms_out) {
+        for (int rep = 0; rep < 2 && err == cudaSuccess; ++rep) {
+            err = cudaEventRecord(ea, e->stream);
+            if (err == cudaSuccess)
+                err = body();
+            if (err == cudaSuccess)
+                err = cudaEventRecord(eb, e->stream);
+            if (err == cudaSuccess)
+                err = cudaEventSynchronize(eb);
+            float ms = 0;
+            if (err == cudaSuccess && rep == 1 && cudaEventElapsedTime(&ms, ea, eb) == cudaSuccess)
+                *ms_out = ms;
+        }
+    };
+    std::vector<isg_ensemble_tuning> cands;
+    isg_ensemble_tuning pick{};
+    pick.threads_per_cta = e->threads;
+    pick.half_teams = e->teams ? 1 : 0;
+    double best_a = 0.0, best_b = 0.0;
+    // part 0: the persistent shared-memory kernel -- CTA size, half-CTA
+    // teams, sweeps per launch
+    if (e->n_smem > 0) {
+        best_a = 1e300;
+        const int threads_c[3] = {256, 512, 1024};
+        const bool can_split = e->split_from_teams < e->n_smem;
+        const int64_t spl_c[2] = {0, std::max<int64_t>(1, sweeps / 5)};
+        for (int ti = 0; ti < 3 && err == cudaSuccess; ++ti)
+            for (int teams = can_split ? 1 : 0; teams >= 0 && err == cudaSuccess; --teams)
+                for (int si = 0; si < 2 && err == cudaSuccess; ++si) {
+                    e->threads = threads_c[ti];
+                    e->teams = teams != 0;
+                    if (apply_shape(e) != ISG_OK) {
+                        err = cudaErrorInvalidValue;
+                        break;
+                    }
+                    const int64_t k = spl_c[si] > 0 ? std::min(spl_c[si], sweeps) : sweeps;
+                    double ms = -1.0;
+                    timed([&]() -> cudaError_t {
+                        int ci = 0;
+                        for (int64_t c0 = 0; c0 < sweeps; c0 += k, ++ci) {
+                            EnsArgs a{};
+                            a.items = items;
+                            a.order = e->d_order;
+                            a.n_order = e->n_smem;
+                            a.counter = e->d_counter + (ci % kMaxLaunches);
+                            a.ithr = e->d_ithr + c0;
+                            a.btab = e->d_btab ? e->d_btab + c0 : nullptr;
+                            a.rec_ring = e->rec_ring;
+                            a.row_bytes = e->row_bytes;
+                            a.rec_cap = (int32_t)e->rec_cap;
+                            a.t0 = (uint32_t)c0;
+                            a.nsweeps = (int32_t)std::min(k, sweeps - c0);
+                            a.half_words = e->half_words;
+                            a.split_from = e->split_from;
+                            e->h_args[ci % kMaxLaunches] = a;
+                            cudaError_t x = cudaMemcpyAsync(e->d_args + (ci % kMaxLaunches), &e->h_args[ci % kMaxLaunches],
+                                                            sizeof(EnsArgs), cudaMemcpyHostToDevice, e->stream);
+                            if (x == cudaSuccess)
+                                x = cudaMemsetAsync(e->d_counter + (ci % kMaxLaunches), 0, sizeof(int32_t), e->stream);
+                            if (x != cudaSuccess)
+                                return x;
+                            k_ensemble<<<e->blocks, e->threads, e->smem, e->stream>>>(e->d_args + (ci % kMaxLaunches));
+                            x = cudaGetLastError();
+                            if (x == cudaSuccess && ci % kMaxLaunches == kMaxLaunches - 1)
+                                x = cudaStreamSynchronize(e->stream);  // pinned arguments reused
+                            if (x != cudaSuccess)
+                                return x;
+                        }
+                        return cudaSuccess;
+                    }, &ms);
+                    isg_ensemble_tuning c{};
+                    c.threads_per_cta = e->threads;
+                    c.half_teams = teams;
+                    c.sweeps_per_launch = spl_c[si];
+                    c.ms = ms;
+                    c.part = 0;
+                    cands.push_back(c);
+                    if (ms >= 0 && ms < best_a) {
+                        best_a = ms;
+                        pick.threads_per_cta = c.threads_per_cta;
+                        pick.half_teams = c.half_teams;
+                        pick.sweeps_per_launch = c.sweeps_per_launch;
+                    }
+                }
+    }
+    // part 1: the multi-lattice launches of the large replicas -- words per
+    // thread and band rows
+    if (!e->groups.empty() && err == cudaSuccess) {
+        best_b = 1e300;
+        const int V_c[4] = {0, 1, 2, 4};
+        const int H_c[4] = {0, 16, 32, 64};
+        for (int vi = 0; vi < 4 && err == cudaSuccess; ++vi)
+            for (int hi = 0; hi < 4 && err == cudaSuccess; ++hi) {
+                double ms = -1.0;
+                timed([&]() -> cudaError_t {
+                    for (int64_t i = 0; i < sweeps; ++i)
+                        for (int c = 0; c < 2; ++c)
+                            for (size_t g = 0; g < e->groups.size(); ++g) {
+                                const auto &gr = e->groups[g];
+                                const cudaError_t x = launch_half_sweep_multi(
+                                    gr.model, gr.L, gplanes[g].data(), gr.seeds.data(),
+                                    (int)gplanes[g].size(), (uint32_t)i, c, e->h_ithr[i],
+                                    e->h_btab ? &e->h_btab[i] : nullptr, e->stream, V_c[vi], H_c[hi]);
+                                if (x != cudaSuccess)
+                                    return x;
+                            }
+                    return cudaSuccess;
+                }, &ms);
+                isg_ensemble_tuning c{};
+                c.threads_per_cta = pick.threads_per_cta;
+                c.half_teams = pick.half_teams;
+                c.sweeps_per_launch = pick.sweeps_per_launch;
+                c.multi_words = V_c[vi];
+                c.multi_band = H_c[hi];
+                c.ms = ms;
+                c.part = 1;
+                cands.push_back(c);
+                if (ms >= 0 && ms < best_b) {
+                    best_b = ms;
+                    pick.multi_words = V_c[vi];
+                    pick.multi_band = H_c[hi];
+                }
+            }
+    }
+    if (ea) cudaEventDestroy(ea);
+    if (eb) cudaEventDestroy(eb);
+    cudaStreamSynchronize(e->stream);
     cudaFree(copy);
     cudaFree(items);
-    if (err != cudaSuccess)
+    if (err != cudaSuccess) {
+        e->threads = saved_threads;
+        e->teams = saved_teams;
+        e->sweeps_per_launch = saved_spl;
+        apply_shape(e);
         return ecuda(err, "autotune");
-    e->threads = best;
-    e->blocks = occupancy_blocks(best, e->smem);
-    if (e->exec) {  // the launch shape changed: rebuild the graph next time
-        cudaGraphExecDestroy(e->exec);
-        e->exec = nullptr;
     }
-    if (threads_out)
-        *threads_out = best;
+    e->threads = pick.threads_per_cta;
+    e->teams = pick.half_teams != 0;
+    e->sweeps_per_launch = pick.sweeps_per_launch;
+    e->multi_V = pick.multi_words;
+    e->multi_H = pick.multi_band;
+    s = apply_shape(e);
+    if (s != ISG_OK)
+        return s;
+    pick.ms = best_a + best_b;
+    if (best)
+        *best = pick;
+    const int64_t n = std::min<int64_t>(max_tried, (int64_t)cands.size());
+    for (int64_t i = 0; i < n; ++i)
+        tried[i] = cands[(size_t)i];
+    if (n_tried)
+        *n_tried = (int64_t)cands.size();
     return ISG_OK;
 }
 

@@ -144,9 +144,11 @@ constexpr int kMultiMax = 240;  // lattices per launch: 240 x 100 B of parameter
 // sweep `sweep`, in as few launches as the kernel parameters allow.
 cudaError_t launch_measure_multi(int model, int64_t L, uint32_t *const *planes, uint8_t *const *recs, int n,
                                  int64_t sweep, cudaStream_t st);
+// V_set / H_set: words per thread and band rows (0: chosen from L and n).
 cudaError_t launch_half_sweep_multi(int model, int64_t L, uint32_t *const *planes, const uint64_t *seeds,
                                     int n, uint32_t t, int colour, const IsingThr &ithr,
-                                    const BcTable *btab, cudaStream_t st);
+                                    const BcTable *btab, cudaStream_t st, int V_set = 0,
+                                    int H_set = 0);
 cudaError_t launch_correlation(const Planes &pl, int nr, const int64_t *d_r, unsigned long long *d_out,
                                cudaStream_t st);
 cudaError_t launch_pack(const Planes &pl, const int8_t *d_spins, int32_t *d_bad, cudaStream_t st);

@@ -1073,7 +1073,7 @@ cudaError_t launch_half_sweep(const Planes &pl, int colour, const PhiloxLaunch &
 
 cudaError_t launch_half_sweep_multi(int model, int64_t L, uint32_t *const *planes, const uint64_t *seeds,
                                     int n, uint32_t t, int colour, const IsingThr &ithr,
-                                    const BcTable *btab, cudaStream_t st)
+                                    const BcTable *btab, cudaStream_t st, int V_set, int H_set)
 {
     const int64_t W = L / 64;
     if (injected_launch_failure())
@@ -1086,13 +1086,16 @@ cudaError_t launch_half_sweep_multi(int model, int64_t L, uint32_t *const *plane
             a.planes[i] = planes[i0 + i];
         }
         if (model == 0) {
-            const int V = W % 4 == 0 ? 4 : (W % 2 == 0 ? 2 : 1);
+            const int V = ((V_set == 1 || V_set == 2 || V_set == 4) && W % V_set == 0)
+                              ? V_set : (W % 4 == 0 ? 4 : (W % 2 == 0 ? 2 : 1));
             const int64_t tpr = W / V;
-            // the band height that fills the GPU for one lattice, shortened
-            // by the m lattices of the launch sharing the waves
+            // the band height that fills the GPU for one lattice, taller
+            // while the m lattices of the launch still fill the waves
             int H = sweep_band(L, tpr);
             while (H < 64 && tpr * ((L + 2 * H - 1) / (2 * H)) * m >= 148LL * kSweepMinBlocks * kSweepThreads * 8)
                 H *= 2;
+            if (H_set > 0)
+                H = H_set;
             const dim3 grid(sweep_blocks(L, tpr, H), (unsigned)m);
             if (V == 4)
                 k_ising_half_multi<4><<<grid, kSweepThreads, 0, st>>>(L, colour, H, ithr, a);
@@ -1101,11 +1104,13 @@ cudaError_t launch_half_sweep_multi(int model, int64_t L, uint32_t *const *plane
             else
                 k_ising_half_multi<1><<<grid, kSweepThreads, 0, st>>>(L, colour, H, ithr, a);
         } else {
-            const int V = W % 2 == 0 ? 2 : 1;
+            const int V = ((V_set == 1 || V_set == 2) && W % V_set == 0) ? V_set : (W % 2 == 0 ? 2 : 1);
             const int64_t tpr = W / V;
             int H = sweep_band(L, tpr, kBcMinBlocks, kBcThreads, 2);
             while (H < 64 && tpr * ((L + 2 * H - 1) / (2 * H)) * m >= 148LL * kBcMinBlocks * kBcThreads * 2)
                 H *= 2;
+            if (H_set > 0)
+                H = H_set;
             const int64_t threads = tpr * ((L + H - 1) / H);
             const dim3 grid((unsigned)((threads + kBcThreads - 1) / kBcThreads), (unsigned)m);
             if (V == 2) {

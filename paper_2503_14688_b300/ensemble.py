@@ -65,10 +65,36 @@ class Ensemble:
                                           ctypes.byref(p), ctypes.byref(th)))
         return {"n": n.value, "sweep": t.value, "pending": p.value, "threads": th.value}
 
-    def autotune(self, sweeps: int = 4) -> int:
-        th = ctypes.c_int32()
-        check(self._lib.isg_ensemble_autotune(self._h, sweeps, ctypes.byref(th)))
-        return th.value
+    _TUNING = ("threads_per_cta", "half_teams", "sweeps_per_launch", "multi_words", "multi_band")
+
+    def autotune(self, sweeps: int = 50, with_candidates: bool = False):
+        """isg_ensemble_autotune: the chosen launch shape as a dict (and, with
+        with_candidates, every candidate tried with its time)."""
+        best = _abi.isg_ensemble_tuning()
+        tried = (_abi.isg_ensemble_tuning * 64)()
+        n = ctypes.c_int64()
+        check(self._lib.isg_ensemble_autotune(self._h, int(sweeps), ctypes.byref(best), tried, 64,
+                                              ctypes.byref(n)))
+        out = {k: getattr(best, k) for k in self._TUNING}
+        out["ms"] = best.ms
+        if with_candidates:
+            cands = [{**{k: getattr(tried[i], k) for k in self._TUNING}, "ms": tried[i].ms,
+                      "part": tried[i].part} for i in range(min(n.value, 64))]
+            return out, cands
+        return out
+
+    def tuning(self) -> dict:
+        t = _abi.isg_ensemble_tuning()
+        check(self._lib.isg_ensemble_get_tuning(self._h, ctypes.byref(t)))
+        return {k: getattr(t, k) for k in self._TUNING}
+
+    def set_tuning(self, **kw):
+        t = _abi.isg_ensemble_tuning()
+        cur = self.tuning()
+        cur.update(kw)
+        for k in self._TUNING:
+            setattr(t, k, int(cur[k]))
+        check(self._lib.isg_ensemble_set_tuning(self._h, ctypes.byref(t)))
 
     def read_records(self, rows: Optional[int] = None, with_sums: bool = True) -> List[List[Obs]]:
         """Up to `rows` oldest record rows; row i is a list over replicas."""

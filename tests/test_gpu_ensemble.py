@@ -148,7 +148,7 @@ def test_ensemble_workload_subset_and_xi2(isg, orc):
     seeds = [wl.BASE_SEED + 3 + r for r in range(64)]
     n, k = 300, 100
     ens = isg.Ensemble(Ls, seeds, record_capacity=4)
-    assert ens.autotune(2) in (256, 512, 1024)
+    assert ens.autotune(2)["threads_per_cta"] in (256, 512, 1024)
     ens.init_random()
     ens.sweep(n, beta=wl.BETA_C_ISING, record_every=k)
     rows = ens.read_records()
@@ -184,3 +184,55 @@ def test_ensemble_errors(isg):
     assert e.value.status == -5
     with pytest.raises(isg.IsgError):
         ens.sweep(1, beta=-1.0)
+
+
+def test_every_launch_shape_gives_the_same_replicas(isg):
+    """The launch shape (CTA size, half-CTA teams, sweeps per launch, the
+    multi-lattice words per thread and band rows) never changes a result:
+    every shape below, including launches cut in the middle of a record
+    period (rounded up) and forced multi-lattice shapes, gives each replica
+    exactly the run of the lattice alone; the autotuner's choice is the
+    fastest candidate of each part."""
+    Ls = [64, 320, 1024, 256, 2048, 1536, 2048]
+    models = [0, 1, 0, 1, 0, 0, 1]
+    seeds = [wl.BASE_SEED + 700 + r for r in range(len(Ls))]
+    n, k = 30, 5
+    betas = [0.44 + 0.002 * i for i in range(n)]
+    alone = []
+    for L, m, sd in zip(Ls, models, seeds):
+        lat = isg.Lattice(L, m, seed=sd, record_capacity=n // k)
+        lat.init_random()
+        lat.sweep(n, betas=np.asarray(betas), record_every=k)
+        alone.append((lat.read_records(), lat.get()))
+        lat.close()
+    shapes = [dict(threads_per_cta=256, half_teams=0, sweeps_per_launch=7, multi_words=1, multi_band=16),
+              dict(threads_per_cta=1024, half_teams=1, sweeps_per_launch=0, multi_words=4, multi_band=64),
+              dict(threads_per_cta=512, half_teams=1, sweeps_per_launch=13, multi_words=2, multi_band=32),
+              dict(threads_per_cta=1024, half_teams=0, sweeps_per_launch=1, multi_words=0, multi_band=0)]
+    for shape in shapes:
+        ens = isg.Ensemble(Ls, seeds, models=models, record_capacity=n // k)
+        ens.set_tuning(**shape)
+        assert ens.tuning() == shape
+        ens.init_random()
+        ens.sweep(n, betas=betas, record_every=k)
+        rows = ens.read_records()
+        assert len(rows) == n // k
+        for r, (recs, s) in enumerate(alone):
+            for i, row in enumerate(rows):
+                _same_obs(row[r], recs[i])
+            assert np.array_equal(ens.get(r), s), (shape, r)
+        ens.close()
+    ens = isg.Ensemble(Ls, seeds, models=models)
+    ens.init_random()
+    best, cands = ens.autotune(4, with_candidates=True)
+    part0 = [c for c in cands if c["part"] == 0]
+    part1 = [c for c in cands if c["part"] == 1]
+    assert len(part0) == 12 and len(part1) == 16
+    f0 = min(part0, key=lambda c: c["ms"])
+    f1 = min(part1, key=lambda c: c["ms"])
+    assert (best["threads_per_cta"], best["half_teams"], best["sweeps_per_launch"]) == \
+        (f0["threads_per_cta"], f0["half_teams"], f0["sweeps_per_launch"])
+    assert (best["multi_words"], best["multi_band"]) == (f1["multi_words"], f1["multi_band"])
+    with pytest.raises(isg.IsgError):
+        ens.set_tuning(threads_per_cta=300)
+    ens.close()

@@ -1,6 +1,6 @@
 """Parity of the replica-ensemble workload in the launch configuration the
 benchmark times: 4096 Ising replicas with L drawn from {64, ..., 1024},
-seeds base + 3 + r, hot start at beta_c, CTA size autotuned, 4 warm-up
+seeds base + 3 + r, hot start at beta_c, launch shape autotuned, 4 warm-up
 sweeps, then 10^4 sweeps in one persistent launch with records every 1000.
 
 * every replica: its record after the first 100 sweeps (B, M, Q, R, C) equals
@@ -66,7 +66,7 @@ def test_bench_configuration_sampled_replicas(isg, orc):
     seeds = [wl.BASE_SEED + 3 + r for r in range(N_REP)]
     ens = isg.Ensemble(Ls, seeds, record_capacity=SWEEPS // EVERY + 1)
     ens.init_random()
-    assert ens.autotune(4) in (256, 512, 1024)
+    assert ens.autotune(50)["threads_per_cta"] in (256, 512, 1024)
     ens.sweep(WARM, beta=wl.BETA_C_ISING)
     ens.sweep(SWEEPS, beta=wl.BETA_C_ISING, record_every=EVERY)
     rows = ens.read_records()
