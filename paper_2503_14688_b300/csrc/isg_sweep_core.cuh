@@ -103,12 +103,14 @@ __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uin
 //
 // The six planes g0..g2, p, n, g3 are known before the random numbers.
 // Their bits become one byte per site -- plane bits at byte bits 2..7, so
-// the byte is already the entry's offset -- by transposing the bit matrix
-// (8 plane words x 32 sites) into 8 words of 4 site bytes: five exchange
-// stages, each swapping one bit of the word index with one bit of the bit
-// position between pairs of words.  Word i of the result then holds sites
-// 4i .. 4i+3 (one Philox call), byte k being site 4i + k.  Per site one byte
-// permute joins the index byte with b at bit 8.
+// the byte is already the entry's offset -- by transposing, within each byte
+// column, the bit matrix of 8 plane words x 32 sites: three exchange stages,
+// each swapping one bit of the word index with one bit of the bit position
+// between pairs of words.  Site s = 4i + k (Philox call i, output word k)
+// then sits in word 2k + (i & 1), byte i >> 1.  Per site one byte permute
+// joins the index byte with b at bit 8.  (Two more stages that gathered each
+// call's four sites into one word cost 16 byte permutes per word for
+// nothing: the byte permute picks any byte of any word.)
 
 // Exchange between words a (index bit 0) and c (index bit 1) of the
 // position bit of value d (mask m: positions where that bit is 0): a's bits
@@ -121,42 +123,23 @@ __device__ __forceinline__ void bit_exchange(uint32_t &a, uint32_t &c, int d, ui
     a ^= t << d;
 }
 
-// The same for position bit 4 (halves) and 3 (bytes), by byte permutes.
-__device__ __forceinline__ void half_exchange(uint32_t &a, uint32_t &c)
-{
-    const uint32_t lo = __byte_perm(a, c, 0x5410u);
-    c = __byte_perm(a, c, 0x7632u);
-    a = lo;
-}
-
-__device__ __forceinline__ void byte_exchange(uint32_t &a, uint32_t &c)
-{
-    const uint32_t ev = __byte_perm(a, c, 0x6240u);
-    c = __byte_perm(a, c, 0x7351u);
-    a = ev;
-}
-
-// Index bytes of the 32 sites: out[i] byte k = site 4i + k, bits 2..7 =
-// (g0, g1, g2, p, n, g3).  Word index bits start as the byte bit each plane
-// is headed for (in the order the stages leave them: plane word j ends at
-// byte bit 4 (j & 1) + 2 ((j >> 2) & 1) + ((j >> 1) & 1), so words 0 and 2,
-// headed for bits 0 and 1, are zero).
+// Index bytes of the 32 sites: site 4i + k in byte i >> 1 of o[2k + (i & 1)],
+// bits 2..7 = (g0, g1, g2, p, n, g3).  The word index starts as the byte bit
+// each plane is headed for, in the order the stages leave it (plane word j
+// ends at byte bit 4 (j & 1) + 2 ((j >> 2) & 1) + ((j >> 1) & 1)), so words
+// 0 and 2, headed for bits 0 and 1, start at zero.
 __device__ __forceinline__ void bc_index_bytes(uint32_t g0, uint32_t g1, uint32_t g2, uint32_t g3,
                                                uint32_t p, uint32_t n, uint32_t (&o)[8])
 {
-    o[0] = 0u;
     o[1] = g2;
-    o[2] = 0u;
     o[3] = p;
-    o[4] = g0;
     o[5] = n;
-    o[6] = g1;
     o[7] = g3;
-    // word bit 2 <-> position bit 1 (words 0 and 2 are zero)
-    o[0] = (o[4] << 2) & 0xCCCCCCCCu;
-    o[4] &= 0xCCCCCCCCu;
-    o[2] = (o[6] << 2) & 0xCCCCCCCCu;
-    o[6] &= 0xCCCCCCCCu;
+    // word bit 2 <-> position bit 1 (the partners of g0 and g1 are zero)
+    o[0] = (g0 << 2) & 0xCCCCCCCCu;
+    o[4] = g0 & 0xCCCCCCCCu;
+    o[2] = (g1 << 2) & 0xCCCCCCCCu;
+    o[6] = g1 & 0xCCCCCCCCu;
     bit_exchange(o[1], o[5], 2, 0x33333333u);
     bit_exchange(o[3], o[7], 2, 0x33333333u);
     // word bit 1 <-> position bit 0
@@ -164,16 +147,6 @@ __device__ __forceinline__ void bc_index_bytes(uint32_t g0, uint32_t g1, uint32_
     bit_exchange(o[1], o[3], 1, 0x55555555u);
     bit_exchange(o[4], o[6], 1, 0x55555555u);
     bit_exchange(o[5], o[7], 1, 0x55555555u);
-    // word bit 2 <-> position bit 4
-    half_exchange(o[0], o[4]);
-    half_exchange(o[1], o[5]);
-    half_exchange(o[2], o[6]);
-    half_exchange(o[3], o[7]);
-    // word bit 1 <-> position bit 3
-    byte_exchange(o[0], o[2]);
-    byte_exchange(o[1], o[3]);
-    byte_exchange(o[4], o[6]);
-    byte_exchange(o[5], o[7]);
     // word bit 0 <-> position bit 2
     bit_exchange(o[0], o[1], 4, 0x0F0F0F0Fu);
     bit_exchange(o[2], o[3], 4, 0x0F0F0F0Fu);
@@ -219,8 +192,10 @@ __device__ __forceinline__ void bc_word_update(uint32_t &n, uint32_t &p, const u
         philox_site4(pc, wp, (uint32_t)q0 + i, r[0], r[1], r[2], r[3]);
 #pragma unroll
         for (int kk = 3; kk >= 0; --kk) {
-            // byte kk of idx[i] (the site's entry offset) and bit 0 of u (b) at bit 8
-            const uint32_t off = __byte_perm(idx[i], r[kk], 0x0040u | (uint32_t)kk) & 0x1FCu;
+            // the site's entry offset (byte i >> 1 of idx[2 kk + (i & 1)]) and
+            // bit 0 of u (b) at bit 8
+            const uint32_t off =
+                __byte_perm(idx[2 * kk + (i & 1)], r[kk], 0x0040u | (uint32_t)(i >> 1)) & 0x1FCu;
             const uint32_t thr = *reinterpret_cast<const uint32_t *>(thr_bytes + off);
             if (kFull)
                 acc = shift_in_not_below(acc, thr, r[kk]);       // + (entry >= u): accept
