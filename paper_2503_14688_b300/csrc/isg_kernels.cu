@@ -208,7 +208,8 @@ __device__ __forceinline__ void ising_half_band(uint32_t g, uint32_t *__restrict
     if (y0 >= Li)
         return;
     const uint32_t y1 = y0 + H < Li ? y0 + H : Li;
-    const uint64_t qrow = (uint64_t)(Wi * 8);  // L / 8 Philox counters per row
+    // L / 8 Philox counters per row (the periodic lattice has Li = L rows)
+    const uint64_t qrow = kWrap ? (uint64_t)(Li / 8) : (uint64_t)(Wi * 8);
     // edge words of the two parities (periodic in the row)
     const uint32_t e_left = w0 == 0 ? Wi - 1 : w0 - 1;
     const uint32_t e_right = w0 + V == Wi ? 0 : w0 + V;
@@ -292,7 +293,8 @@ __device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ t
     if (y0 >= Li)
         return;
     const uint32_t y1 = y0 + H < Li ? y0 + H : Li;
-    const uint64_t qrow = (uint64_t)(Wi * 8);  // L / 8 Philox counters per row
+    // L / 8 Philox counters per row (the periodic lattice has Li = L rows)
+    const uint64_t qrow = kWrap ? (uint64_t)(Li / 8) : (uint64_t)(Wi * 8);
     const uint32_t e_left = w0 == 0 ? Wi - 1 : w0 - 1;
     const uint32_t e_right = w0 + V == Wi ? 0 : w0 + V;
     const int64_t dpn = np_plane - nn_plane, dtp = tp_plane - tn_plane;  // occupancy -> sign plane
