@@ -343,11 +343,29 @@ def served_bench(n_req=2000, n_saturated=200, load=0.9, chunk=100, max_active=48
         torch.cuda.synchronize()
         ref_rate[model] = 32768.0 ** 2 * 50 / (a.elapsed_time(b) * 1e-3)
         lat.close()
-    alone = np.array([f / ref_rate[r["model"]] for f, r in zip(flips, reqs)])  # s at full rate
+    # each request's time alone on the idle GPU: its flips at the measured
+    # single-lattice rate of its own (model, L), as isg_sweep runs it
+    own_rate = {}
+    for model, L in sorted({(r["model"], r["L"]) for r in reqs}):
+        k = int(min(2000, max(20, 5e9 / float(L) ** 2)))
+        lat = P.Lattice(L, model, seed=wl.BASE_SEED + 6)
+        lat.init_random()
+        beta = wl.BETA_C_ISING if model == wl.ISING else 1.0 / wl.T_C_BLUME_CAPEL
+        lat.sweep(2, beta=beta)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        lat.sweep(k, beta=beta)
+        b.record()
+        torch.cuda.synchronize()
+        own_rate[(model, L)] = float(L) ** 2 * k / (a.elapsed_time(b) * 1e-3)
+        lat.close()
+    alone = np.array([f / own_rate[(r["model"], r["L"])] for f, r in zip(flips, reqs)])
+    full = np.array([f / ref_rate[r["model"]] for f, r in zip(flips, reqs)])  # at the L=32768 rate
 
     sat = reqs[:n_saturated]
     sat_total = float(flips[:n_saturated].sum())
-    ref = sat_total / float(alone[:n_saturated].sum())
+    ref = sat_total / float(full[:n_saturated].sum())
     _, span0 = run(sat, [0.0] * len(sat))
     capacity = sat_total / span0  # flips/s with the queue always full
     total = float(flips.sum())
@@ -369,10 +387,17 @@ def served_bench(n_req=2000, n_saturated=200, load=0.9, chunk=100, max_active=48
                         "value": total / span / 1e9, "unit": UNIT,
                         "p50_s": float(np.percentile(lat, 50)),
                         "p99_s": float(np.percentile(lat, 99)), "makespan_s": span,
+                        "slowdown_basis": "latency / the request's time alone on the idle GPU "
+                                          "(its flips at the single-lattice rate of its model and L)",
                         "slowdown_p50": float(np.percentile(slow, 50)),
                         "slowdown_p99": float(np.percentile(slow, 99)),
                         "slowdown_mean": float(slow.mean()),
-                        "slowdown_processor_sharing": 1.0 / (1.0 - load)},
+                        "slowdown_p50_by_L": {str(L): float(np.percentile(
+                            slow[[r["L"] == L for r in reqs]], 50))
+                            for L in sorted({r["L"] for r in reqs})},
+                        "slowdown_processor_sharing": 1.0 / (1.0 - load),
+                        "alone_rate_by_model_L": {f"{m}:{L}": v / 1e9
+                                                  for (m, L), v in sorted(own_rate.items())}},
             "total_flips": total}
 
 

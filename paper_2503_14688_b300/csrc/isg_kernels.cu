@@ -380,6 +380,8 @@ __global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
 // read out and added atomically.
 // ---------------------------------------------------------------------------
 constexpr int kMeasureBand = 8192;  // rows per band at most
+// blocks per SM the launch bounds ask for, per model
+constexpr int kMeasureBlocksIsing = 3, kMeasureBlocksBc = 2;
 constexpr int kHighBits = 10;       // high counter: multiples of 16 up to 16 * 1023
 
 struct ColumnCounter {
@@ -495,82 +497,107 @@ __device__ __forceinline__ void measure_band(const uint32_t *base, int64_t L, in
     const uint32_t *p0c = p0 + wc, *p1c = p1 + wc;
     const uint32_t *n0c = n0 + wc, *n1c = n1 + wc;
     const int64_t off_l = wl - wc, off_r = wr - wc;
-    const uint32_t *t1 = p1c + y0 * W, *t0 = p0c + y0 * W;  // row y0 + r0 + 4 g, advanced by 4 rows
-    for (int r0 = 0; r0 < rows; r0 += 16) {
-#pragma unroll 1
-        for (int g = 0; g < 4; ++g, t1 += 4 * W, t0 += 4 * W) {
-            const int64_t yg = y0 + r0 + 4 * g;
-            const bool last = kWrap && yg + 4 == L;  // row yg + 3 wraps to row 0
-            uint32_t Tp[4], Dp[4], Ep[4], Tn[4], Dn[4], En[4];
-            if (active) {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const uint32_t *down = (r == 3 && last) ? p0c : t0 + (r + 1) * W;
-                    const uint32_t *edge = t0 + r * W + ((r & 1) ? off_l : off_r);
-                    Tp[r] = __ldg(t1 + r * W);
-                    Dp[r] = __ldg(down);
-                    Ep[r] = __ldg(edge);
-                    if (MODEL == 1) {
-                        const int64_t d_nb = n0c - p0c;  // occupancy planes: fixed offset
-                        Tn[r] = __ldg(t1 + r * W + (n1c - p1c));
-                        Dn[r] = __ldg(down + d_nb);
-                        En[r] = __ldg(edge + d_nb);
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    Tp[r] = Dp[r] = Ep[r] = Tn[r] = Dn[r] = En[r] = 0;
-            }
-            uint32_t evp[4], odp[4], evm[4], odm[4];
+    const uint32_t *t1 = p1c + y0 * W, *t0 = p0c + y0 * W;  // the band's first row
+    // The band is walked in 4-row groups, all loads of a group (Ising: of
+    // two groups) issued before any is used.
+    struct Group {
+        uint32_t Tp[4], Dp[4], Ep[4], Tn[4], Dn[4], En[4];
+    };
+    const int ngroups = rows / 4;  // even: a band has a multiple of 16 rows
+    auto load = [&](Group &G, int gg) {
+        const uint32_t *g1 = t1 + (int64_t)(4 * gg) * W, *g0p = t0 + (int64_t)(4 * gg) * W;
+        const bool last = kWrap && y0 + 4 * gg + 4 == L;  // row + 3 wraps to row 0
+        if (active) {
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
-                const bool odd = r & 1;
-                const uint32_t Xp = odd ? (Sp << 1) | (Ep[r] >> 31) : (Sp >> 1) | (Ep[r] << 31);
-                int rowpart;
-                if (MODEL == 0) {
-                    const uint32_t T = Tp[r];
-                    const int anti = __popc(T ^ Up) + __popc(T ^ Dp[r]) + __popc(T ^ Sp) +
-                                     __popc(T ^ Xp);
-                    accB += 128 - 2 * anti;
-                    rowpart = 2 * (__popc(T) + __popc(Sp)) - 64;
-                    evp[r] = odd ? T : Sp;
-                    odp[r] = odd ? Sp : T;
-                } else {
-                    const uint32_t Xn = odd ? (Sn << 1) | (En[r] >> 31) : (Sn >> 1) | (En[r] << 31);
-                    const uint32_t Tn_ = Tn[r], Tp_ = Tp[r];
-                    const uint32_t nb[4] = {Un, Dn[r], Sn, Xn}, pb[4] = {Up, Dp[r], Sp, Xp};
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        const uint32_t both = Tn_ & nb[k];
-                        accB += __popc(both) - 2 * __popc(both & (Tp_ ^ pb[k]));
-                    }
-                    const uint32_t plus1 = Tn_ & Tp_, minus1 = Tn_ & ~Tp_;
-                    const uint32_t plus0 = Sn & Sp, minus0 = Sn & ~Sp;
-                    rowpart = __popc(plus1) + __popc(plus0) - __popc(minus1) - __popc(minus0);
-                    accQ += __popc(Tn_) + __popc(Sn);
-                    evp[r] = odd ? plus1 : plus0;
-                    odp[r] = odd ? plus0 : plus1;
-                    evm[r] = odd ? minus1 : minus0;
-                    odm[r] = odd ? minus0 : minus1;
-                    Un = Sn;
-                    Sn = Dn[r];
+                const uint32_t *down = (r == 3 && last) ? p0c : g0p + (r + 1) * W;
+                const uint32_t *edge = g0p + r * W + ((r & 1) ? off_l : off_r);
+                G.Tp[r] = __ldg(g1 + r * W);
+                G.Dp[r] = __ldg(down);
+                G.Ep[r] = __ldg(edge);
+                if (MODEL == 1) {
+                    const int64_t d_nb = n0c - p0c;  // occupancy planes: fixed offset
+                    G.Tn[r] = __ldg(g1 + r * W + (n1c - p1c));
+                    G.Dn[r] = __ldg(down + d_nb);
+                    G.En[r] = __ldg(edge + d_nb);
                 }
-                if (!active)
-                    rowpart = 0;
-                accM += rowpart;
-                const int rs = __reduce_add_sync(0xFFFFFFFFu, rowpart);
-                if ((threadIdx.x & 31) == 0)
-                    atomicAdd(&s_row[r0 + 4 * g + r], rs);
-                Up = Sp;
-                Sp = Dp[r];
             }
-            cc_add4(ce_p, evp[0], evp[1], evp[2], evp[3], g);
-            cc_add4(co_p, odp[0], odp[1], odp[2], odp[3], g);
-            if (MODEL == 1) {
-                cc_add4(ce_m, evm[0], evm[1], evm[2], evm[3], g);
-                cc_add4(co_m, odm[0], odm[1], odm[2], odm[3], g);
+        } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                G.Tp[r] = G.Dp[r] = G.Ep[r] = G.Tn[r] = G.Dn[r] = G.En[r] = 0;
+        }
+    };
+    auto process = [&](const Group &G, int gg) {
+        uint32_t evp[4], odp[4], evm[4], odm[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const bool odd = r & 1;
+            const uint32_t Xp = odd ? (Sp << 1) | (G.Ep[r] >> 31) : (Sp >> 1) | (G.Ep[r] << 31);
+            int rowpart;
+            if (MODEL == 0) {
+                const uint32_t T = G.Tp[r];
+                const int anti = __popc(T ^ Up) + __popc(T ^ G.Dp[r]) + __popc(T ^ Sp) +
+                                 __popc(T ^ Xp);
+                accB += 128 - 2 * anti;
+                rowpart = 2 * (__popc(T) + __popc(Sp)) - 64;
+                evp[r] = odd ? T : Sp;
+                odp[r] = odd ? Sp : T;
+            } else {
+                const uint32_t Xn = odd ? (Sn << 1) | (G.En[r] >> 31) : (Sn >> 1) | (G.En[r] << 31);
+                const uint32_t Tn_ = G.Tn[r], Tp_ = G.Tp[r];
+                const uint32_t nb[4] = {Un, G.Dn[r], Sn, Xn}, pb[4] = {Up, G.Dp[r], Sp, Xp};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const uint32_t both = Tn_ & nb[k];
+                    accB += __popc(both) - 2 * __popc(both & (Tp_ ^ pb[k]));
+                }
+                const uint32_t plus1 = Tn_ & Tp_, minus1 = Tn_ & ~Tp_;
+                const uint32_t plus0 = Sn & Sp, minus0 = Sn & ~Sp;
+                rowpart = __popc(plus1) + __popc(plus0) - __popc(minus1) - __popc(minus0);
+                accQ += __popc(Tn_) + __popc(Sn);
+                evp[r] = odd ? plus1 : plus0;
+                odp[r] = odd ? plus0 : plus1;
+                evm[r] = odd ? minus1 : minus0;
+                odm[r] = odd ? minus0 : minus1;
+                Un = Sn;
+                Sn = G.Dn[r];
             }
+            if (!active)
+                rowpart = 0;
+            accM += rowpart;
+            const int rs = __reduce_add_sync(0xFFFFFFFFu, rowpart);
+            if ((threadIdx.x & 31) == 0)
+                atomicAdd(&s_row[4 * gg + r], rs);
+            Up = Sp;
+            Sp = G.Dp[r];
+        }
+        const int g = gg & 3;  // group within its 16-row block
+        cc_add4(ce_p, evp[0], evp[1], evp[2], evp[3], g);
+        cc_add4(co_p, odp[0], odp[1], odp[2], odp[3], g);
+        if (MODEL == 1) {
+            cc_add4(ce_m, evm[0], evm[1], evm[2], evm[3], g);
+            cc_add4(co_m, odm[0], odm[1], odm[2], odm[3], g);
+        }
+    };
+    Group A, B;
+    if (MODEL == 0) {
+        // two groups' loads go out together, then both are processed (a
+        // prefetch of the next pair while processing was 17% slower)
+#pragma unroll 1
+        for (int gg = 0; gg < ngroups; gg += 2) {
+            load(A, gg);
+            load(B, gg + 1);
+            process(A, gg);
+            process(B, gg + 1);
+        }
+    } else {
+        // Blume-Capel loads twice the words per group: one group at a
+        // time, so that the kernel stays within its registers
+#pragma unroll 1
+        for (int gg = 0; gg < ngroups; ++gg) {
+            load(A, gg);
+            process(A, gg);
         }
     }
     if (!active)
@@ -611,7 +638,7 @@ __device__ __forceinline__ void measure_band(const uint32_t *base, int64_t L, in
 }
 
 template <int MODEL>
-__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
+__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? kMeasureBlocksIsing : kMeasureBlocksBc)
     k_measure(Planes pl, int H, int64_t *__restrict__ rec_hdr, int32_t *__restrict__ R,
               int32_t *__restrict__ C, int64_t sweep)
 {
@@ -628,7 +655,7 @@ struct MeasureMultiArgs {
 };
 
 template <int MODEL>
-__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
+__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? kMeasureBlocksIsing : kMeasureBlocksBc)
     k_measure_multi(int64_t L, int H, int64_t sweep, const __grid_constant__ MeasureMultiArgs a)
 {
     __shared__ int32_t s_row[kMeasureBand];
@@ -682,7 +709,7 @@ __global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
 }
 
 template <int MODEL>
-__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? 4 : 2)
+__global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? kMeasureBlocksIsing : kMeasureBlocksBc)
     k_measure_slab(const uint32_t *base, int64_t rows, int64_t W, int H, int64_t *__restrict__ rec_hdr,
                    int32_t *__restrict__ R, int32_t *__restrict__ C, int64_t sweep)
 {
