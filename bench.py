@@ -12,12 +12,14 @@ quench to beta_c; the lattice is far larger than L2, so no flush is needed
 between steps.  The line carries the other large-quench lattice, Blume-Capel
 Delta = 0 at L = 2^19 (64 GiB), measured the same way (`blume_capel_large`),
 the replica ensemble (`batched`), the served request stream (`served`), the
-pre-cooling scan, Swendsen-Wang and the oracle on the host cores.
+pre-cooling scan, the row-slab decomposition on one GPU (`decomposition`),
+Swendsen-Wang and the oracle on the host cores.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload ising_large|blume_capel_large|ising_small|blume_capel_parity]
                     [--served-requests N] [--served-saturated N]
                     [--no-bc] [--no-batched] [--no-served] [--no-precool] [--no-sw]
+                    [--no-decomposition]
                     [--no-cpu-baseline] [--no-calib]
 
 Prints one JSON line.  `value` is the device-timed throughput (spin-flip
@@ -256,6 +258,52 @@ def precool_bench(n_rep=4096):
             "f_star": res["f_star"], "f_star_err": res["f_star_err"], "f_star_paper": 0.59,
             "ensemble_flips_per_ns": res["ensemble_flips_per_ns"],
             "seconds": time.perf_counter() - t0}
+
+
+def decomposition_bench(L=1 << 19, P=4, sweeps=6):
+    """The row-slab domain decomposition on one GPU: one Ising lattice cut
+    into P slabs in this process (halo rows copied device to device before
+    every half-sweep), against the same lattice swept whole.  Several GPUs
+    would each hold one slab; here the slabs share one."""
+    import torch
+
+    import paper_2503_14688_b300 as P_
+    from paper_2503_14688_b300 import decomposition as dd
+
+    beta = wl.BETA_C_ISING
+    parts = dd.partition(L, P)
+    slabs = {r: dd.Slab(wl.ISING, L, y0, rows, wl.BASE_SEED + 8) for r, (y0, rows) in enumerate(parts)}
+    for sl in slabs.values():
+        sl.init_random()
+    run = dd.Decomposition(slabs, dd.LocalExchange(P))
+    run.sweep(2, beta=beta)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    run.sweep(sweeps, beta=beta)
+    torch.cuda.synchronize()
+    slab_s = time.perf_counter() - t0
+    rec = run.record()
+    for sl in slabs.values():
+        sl.close()
+    lat = P_.Lattice(L, wl.ISING, seed=wl.BASE_SEED + 8)
+    lat.init_random()
+    lat.sweep(2, beta=beta)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat.sweep(sweeps, beta=beta)
+    torch.cuda.synchronize()
+    whole_s = time.perf_counter() - t0
+    wrec = lat.measure()
+    lat.close()
+    sites = float(L) ** 2
+    return {"workload": f"Ising L={L} as {P} row slabs in one process, halos exchanged device to "
+                        f"device before every half-sweep, {sweeps} sweeps (host-timed)",
+            "slabs": [r for _, r in parts],
+            "value": sites * sweeps / slab_s / 1e9, "unit": UNIT,
+            "whole_lattice": sites * sweeps / whole_s / 1e9,
+            "ratio": whole_s / slab_s,
+            "halo_bytes_per_half_sweep_per_slab": 2 * L // 16,
+            "same_record_as_whole": (rec.B, rec.M, rec.Q) == (wrec.B, wrec.M, wrec.Q)}
 
 
 def sw_bench(Ls=(4096, 16384), reps=20):
@@ -660,6 +708,8 @@ def run_ours(args, w):
                                           n_saturated=args.served_saturated)
         if not args.no_precool and world == 1:
             line["precool"] = precool_bench()
+        if not args.no_decomposition and world == 1:
+            line["decomposition"] = decomposition_bench()
         if not args.no_sw and world == 1:
             line["swendsen_wang"] = sw_bench()
         if not args.no_cpu_baseline:
@@ -691,6 +741,8 @@ def main():
     ap.add_argument("--served-saturated", type=int, default=200,
                     help="requests (the stream's first) of the saturated capacity leg")
     ap.add_argument("--no-served", action="store_true", help="skip the served stream")
+    ap.add_argument("--no-decomposition", action="store_true",
+                    help="skip the row-slab decomposition sub-object")
     ap.add_argument("--no-bc", action="store_true",
                     help="skip the Blume-Capel L=2^19 single-lattice sub-object")
     ap.add_argument("--no-calib", action="store_true",
