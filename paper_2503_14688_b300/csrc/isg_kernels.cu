@@ -33,7 +33,7 @@ namespace {
 constexpr int kSweepThreads = 128;
 constexpr int kSweepMinBlocks = 10;  // 48 registers: 40 warps per SM
 constexpr int kBcThreads = 256;
-constexpr int kBcMinBlocks = 3;      // 80 registers: 24 warps per SM
+constexpr int kBcMinBlocks = 2;      // 128 registers: 16 warps per SM, two words interleaved
 constexpr int kMeasureThreads = 256;
 
 template <int V>
@@ -317,12 +317,24 @@ __device__ __forceinline__ void bc_half_band(int64_t g, uint32_t *__restrict__ t
         const Words<V> Xp = side_words<V>(Sp, __ldg(edge + dpn), parity);
         Words<V> Tn = load_words_rw<V>(trow + w0);
         Words<V> Tp = load_words_rw<V>(trow + dtp + w0);
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-            const uint32_t nbn[4] = {Un.v[v], Dn.v[v], Sn.v[v], Xn.v[v]};
-            const uint32_t nbp[4] = {Up.v[v], Dp.v[v], Sp.v[v], Xp.v[v]};
-            const uint64_t q0 = (uint64_t)yg * qrow + 8u * (uint64_t)(w0 + v);
-            bc_word_update<kFull>(Tn.v[v], Tp.v[v], nbn, nbp, q0, pc, s_thr);
+        if constexpr (V == 2) {
+            // the two words interleaved (bc_word_update2)
+            const uint32_t nbn[2][4] = {{Un.v[0], Dn.v[0], Sn.v[0], Xn.v[0]},
+                                        {Un.v[1], Dn.v[1], Sn.v[1], Xn.v[1]}};
+            const uint32_t nbp[2][4] = {{Up.v[0], Dp.v[0], Sp.v[0], Xp.v[0]},
+                                        {Up.v[1], Dp.v[1], Sp.v[1], Xp.v[1]}};
+            uint32_t nn[2] = {Tn.v[0], Tn.v[1]}, pp[2] = {Tp.v[0], Tp.v[1]};
+            const uint64_t q0 = (uint64_t)yg * qrow + 8u * (uint64_t)w0;
+            bc_word_update2<kFull>(nn, pp, nbn, nbp, q0, q0 + 8u, pc, s_thr);
+            Tn.v[0] = nn[0];
+            Tn.v[1] = nn[1];
+            Tp.v[0] = pp[0];
+            Tp.v[1] = pp[1];
+        } else {
+            const uint32_t nbn[4] = {Un.v[0], Dn.v[0], Sn.v[0], Xn.v[0]};
+            const uint32_t nbp[4] = {Up.v[0], Dp.v[0], Sp.v[0], Xp.v[0]};
+            const uint64_t q0 = (uint64_t)yg * qrow + 8u * (uint64_t)w0;
+            bc_word_update<kFull>(Tn.v[0], Tp.v[0], nbn, nbp, q0, pc, s_thr);
         }
         store_words<V>(trow + w0, Tn);
         store_words<V>(trow + dtp + w0, Tp);
