@@ -31,7 +31,7 @@ namespace isg {
 namespace {
 
 constexpr int kSweepThreads = 128;
-constexpr int kSweepMinBlocks = 10;  // 48 registers: 40 warps per SM
+constexpr int kSweepMinBlocks = 6;   // 80 registers: 24 warps per SM, four words interleaved
 constexpr int kBcThreads = 256;
 constexpr int kBcMinBlocks = 2;      // 128 registers: 16 warps per SM, two words interleaved
 constexpr int kMeasureThreads = 256;
@@ -228,9 +228,7 @@ __device__ __forceinline__ void ising_half_band(uint32_t g, uint32_t *__restrict
         const Words<V> X = side_words<V>(S, edge, parity);
         Words<V> T = load_words_rw<V>(trow + w0);
         const uint64_t qy = (uint64_t)yg * qrow + 8u * w0;
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-            T.v[v] = ising_word_update(T.v[v], U.v[v], D.v[v], S.v[v], X.v[v], qy + 8u * v, pc, thr);
+        ising_words_update<V>(T.v, U.v, D.v, S.v, X.v, qy, pc, thr);  // the V words interleaved
         store_words<V>(trow + w0, T);
         U = S;
         S = D;

@@ -55,9 +55,27 @@ __device__ __forceinline__ PhiloxLaunch philox_consts_device(uint64_t seed, uint
     return pc;
 }
 
-// Ising: new target word.  A site with c anti-aligned neighbours has
-// dE = 8 - 4c (Eq. (1), J = 1): c >= 2 always flips, c = 1 flips iff
-// u < thr4, c = 0 iff u < thr8.
+// Ising flip mask of a target word from its reject masks (bit set iff the
+// site's word is >= thr4 / thr8) and its four neighbour words.  A site with
+// c anti-aligned neighbours has dE = 8 - 4c (Eq. (1), J = 1): c >= 2 always
+// flips, c = 1 flips iff u < thr4, c = 0 iff u < thr8.
+__device__ __forceinline__ uint32_t ising_flips(uint32_t t, uint32_t up, uint32_t dn, uint32_t same,
+                                                uint32_t side, uint32_t r4, uint32_t r8,
+                                                const IsingThr &thr)
+{
+    const uint32_t a4 = ~r4 | thr.full4;
+    const uint32_t a8 = ~r8 | thr.full8;
+    // anti-aligned neighbour indicators and their bit-sliced count
+    const uint32_t a = t ^ up, b = t ^ dn, d = t ^ same, e = t ^ side;
+    const uint32_t s1 = a ^ b ^ d;
+    const uint32_t c1 = (a & b) | (d & (a ^ b));
+    const uint32_t s = s1 ^ e;  // count = s + 2 (c1 + c2)
+    const uint32_t c2 = s1 & e;
+    const uint32_t ge2 = c1 | c2;  // dE <= 0: always flip
+    return ge2 | (~ge2 & ((s & a4) | (~s & a8)));
+}
+
+// Ising: new target word (one word at a time; the shared-memory ensemble).
 __device__ __forceinline__ uint32_t ising_word_update(uint32_t t, uint32_t up, uint32_t dn,
                                                       uint32_t same, uint32_t side, uint64_t q0,
                                                       const PhiloxLaunch &pc, const IsingThr &thr)
@@ -76,17 +94,44 @@ __device__ __forceinline__ uint32_t ising_word_update(uint32_t t, uint32_t up, u
             r8 = shift_in_not_below(r8, r[k], thr.thr8);
         }
     }
-    const uint32_t a4 = ~r4 | thr.full4;
-    const uint32_t a8 = ~r8 | thr.full8;
-    // anti-aligned neighbour indicators and their bit-sliced count
-    const uint32_t a = t ^ up, b = t ^ dn, d = t ^ same, e = t ^ side;
-    const uint32_t s1 = a ^ b ^ d;
-    const uint32_t c1 = (a & b) | (d & (a ^ b));
-    const uint32_t s = s1 ^ e;  // count = s + 2 (c1 + c2)
-    const uint32_t c2 = s1 & e;
-    const uint32_t ge2 = c1 | c2;  // dE <= 0: always flip
-    const uint32_t flip = ge2 | (~ge2 & ((s & a4) | (~s & a8)));
-    return t ^ flip;
+    return t ^ ising_flips(t, up, dn, same, side, r4, r8, thr);
+}
+
+// Ising: N consecutive target words of one row (counters q0, q0 + 8, ...),
+// their Philox calls and compare chains interleaved so that each thread
+// has N independent chains in flight (four words: 1.7% faster than one
+// after another at L = 2^20).
+template <int N>
+__device__ __forceinline__ void ising_words_update(uint32_t (&t)[N], const uint32_t (&up)[N],
+                                                   const uint32_t (&dn)[N], const uint32_t (&same)[N],
+                                                   const uint32_t (&side)[N], uint64_t q0,
+                                                   const PhiloxLaunch &pc, const IsingThr &thr)
+{
+    PhiloxWordPart wp[N];
+    uint32_t r4[N], r8[N];
+#pragma unroll
+    for (int v = 0; v < N; ++v) {
+        wp[v] = philox_word_part(pc, (uint32_t)((q0 + 8u * v) >> 32));
+        r4[v] = r8[v] = 0;
+    }
+#pragma unroll
+    for (int i = 7; i >= 0; --i) {
+        uint32_t r[N][4];
+#pragma unroll
+        for (int v = 0; v < N; ++v)
+            philox_site4(pc, wp[v], (uint32_t)(q0 + 8u * v) + i, r[v][0], r[v][1], r[v][2], r[v][3]);
+#pragma unroll
+        for (int k = 3; k >= 0; --k) {
+#pragma unroll
+            for (int v = 0; v < N; ++v) {
+                r4[v] = shift_in_not_below(r4[v], r[v][k], thr.thr4);
+                r8[v] = shift_in_not_below(r8[v], r[v][k], thr.thr8);
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < N; ++v)
+        t[v] ^= ising_flips(t[v], up[v], dn[v], same[v], side[v], r4[v], r8[v], thr);
 }
 
 __device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &s,
