@@ -70,8 +70,12 @@ PIPE_OPS = {wl.ISING: {"wide": 5.0, "alu": 5.0, "either": 5.0},
 # The kernels fold the launch-uniform parts of Philox's first two rounds:
 # 18 wide multiplies per 4 sites instead of 20.
 WIDE_MUL_PER_SITE_FOLDED = 18 / 4
-DRAM_BYTES_PER_SITE = {wl.ISING: (536.9e6 + 229.4e6) / 2**31,
-                       wl.BLUME_CAPEL: (274.3e6 + 93.5e6) / 2**29}
+# DRAM bytes (read + write) per site of one half-sweep launch, from one ncu
+# capture of the current kernels on a smaller lattice (Ising L = 2^16:
+# 537.98 + 229.27 MB per 2^31 sites; Blume-Capel L = 2^15: 269.83 + 94.14 MB
+# per 2^29 sites), scaled to a full launch by the sites it updates.
+DRAM_BYTES_PER_SITE = {wl.ISING: (537.98e6 + 229.27e6) / 2**31,
+                       wl.BLUME_CAPEL: (269.83e6 + 94.14e6) / 2**29}
 
 
 def _l2_note(lattice_bytes):
