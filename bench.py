@@ -57,16 +57,19 @@ UNIT = "flips/ns"
 #   Ising acceptance: 2 threshold compares + 2 bit inserts; the bit-sliced
 #   neighbour count and flip logic: about 1 per site (30-40 per 32 sites);
 #   total 15;
-#   Blume-Capel: the same Philox plus the spin-1 acceptance (about six
-#   compares over the candidate energies) and the two-plane update: about 25.
-ALG_OPS_PER_SITE = {wl.ISING: 15.0, wl.BLUME_CAPEL: 25.0}
+#   Blume-Capel: the same Philox; per site the table entry's offset (byte
+#   permute + mask), the compare (2) and the proposal bit (1); per 32-site
+#   word the bit-sliced field sum (~30), the transpose of six planes into
+#   index bytes (~56) and the two-plane update (~10), about 3 per site;
+#   total 18 (the shared-memory table load is not an integer op).
+ALG_OPS_PER_SITE = {wl.ISING: 15.0, wl.BLUME_CAPEL: 18.0}
 INT_LANES_PER_SM = 128     # 4 SMSPs x 32 lanes, one warp-instruction per SMSP per clock
 # The same algorithmic counts split by execution pipe (pipe-aware bound):
 # Philox's 5 wide (32x32->64) multiplies per site run on the FMA-heavy pipe,
 # its 5 three-input XORs on the ALU pipe, and the remaining ops (Ising 5,
-# Blume-Capel 15) may issue on either pipe.
+# Blume-Capel 8) may issue on either pipe.
 PIPE_OPS = {wl.ISING: {"wide": 5.0, "alu": 5.0, "either": 5.0},
-            wl.BLUME_CAPEL: {"wide": 5.0, "alu": 5.0, "either": 15.0}}
+            wl.BLUME_CAPEL: {"wide": 5.0, "alu": 5.0, "either": 8.0}}
 # The kernels fold the launch-uniform parts of Philox's first two rounds:
 # 18 wide multiplies per 4 sites instead of 20.
 WIDE_MUL_PER_SITE_FOLDED = 18 / 4
