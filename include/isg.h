@@ -555,10 +555,16 @@ isg_status isg_sw_iterations(const isg_lattice *lat, int64_t *count);
  * allocated and the call reports ISG_ERR_OOM after freeing what it had
  * allocated.  what = ISG_INJECT_LAUNCH: the `after`-th sweep kernel launch
  * (single-lattice, slab, multi-lattice or persistent ensemble / server
- * launch) is skipped and the call reports ISG_ERR_CUDA.  Each injection
- * fires once; after = 0 disarms it.  Process-wide, thread-safe. */
+ * launch) is skipped and the call reports ISG_ERR_CUDA.  what =
+ * ISG_INJECT_WAIT: the `after`-th record pass that streams its rows through
+ * shared memory (lattices with L a multiple of 16384) announces 16 bytes more
+ * than it copies in one block, so that block's bounded waits run out (about
+ * 4 s); the pass marks the record failed and the call that reads it (or
+ * isg_read_records, which drops it) reports ISG_ERR_DEVICE_TIMEOUT.  Each
+ * injection fires once; after = 0 disarms it.  Process-wide, thread-safe. */
 #define ISG_INJECT_ALLOC 1
 #define ISG_INJECT_LAUNCH 2
+#define ISG_INJECT_WAIT 3
 isg_status isg_debug_inject(int32_t what, int64_t after);
 
 /* Energy per spin (-B + Delta Q) / L^2 of one record. */

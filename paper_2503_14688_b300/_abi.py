@@ -21,7 +21,7 @@ ISG_NOALLOC_MAX_L = 1 << 18
 ISG_SW_MAX_L = 32768
 ISG_REQ_QUEUED, ISG_REQ_RUNNING, ISG_REQ_DONE = 0, 1, 2
 ISG_REQ_CANCELLED, ISG_REQ_EXPIRED, ISG_REQ_FAILED = 3, 4, 5
-ISG_INJECT_ALLOC, ISG_INJECT_LAUNCH = 1, 2
+ISG_INJECT_ALLOC, ISG_INJECT_LAUNCH, ISG_INJECT_WAIT = 1, 2, 3
 ISG_ISING = 0
 ISG_BLUME_CAPEL = 1
 

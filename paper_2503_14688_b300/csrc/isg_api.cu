@@ -64,7 +64,7 @@ namespace isg {
 namespace {
 // armed injections: the count of events still to pass before the failing
 // one (0 = disarmed)
-std::atomic<int64_t> g_inject_alloc{0}, g_inject_launch{0};
+std::atomic<int64_t> g_inject_alloc{0}, g_inject_launch{0}, g_inject_wait{0};
 
 bool take(std::atomic<int64_t> &counter)
 {
@@ -96,6 +96,8 @@ cudaError_t dev_malloc_async_raw(void **p, size_t bytes, cudaStream_t st)
 }
 
 bool injected_launch_failure() { return take(g_inject_launch); }
+
+bool injected_wait_failure() { return take(g_inject_wait); }
 
 int32_t report_error(int32_t code, const char *fmt, ...)
 {
@@ -195,6 +197,8 @@ isg_status copy_record(const isg_lattice *lat, const uint8_t *slot, isg_obs *out
 {
     int64_t hdr[4];
     ISG_CUDA(cudaMemcpy(hdr, slot, sizeof(hdr), cudaMemcpyDeviceToHost), "record read");
+    if (hdr[0] == kRecordFailed)
+        return fail(ISG_ERR_DEVICE_TIMEOUT, "the record pass ran out of time waiting for its row copies");
     out->sweep = hdr[0];
     out->B = hdr[1];
     out->M = hdr[2];
@@ -269,6 +273,8 @@ isg_status isg_debug_inject(int32_t what, int64_t after)
         isg::g_inject_alloc.store(after);
     else if (what == ISG_INJECT_LAUNCH)
         isg::g_inject_launch.store(after);
+    else if (what == ISG_INJECT_WAIT)
+        isg::g_inject_wait.store(after);
     else
         return fail(ISG_ERR_INVALID, "unknown injection %d", what);
     return ISG_OK;
@@ -513,6 +519,10 @@ isg_status isg_read_records(isg_lattice *lat, isg_obs *out, int64_t max, int64_t
     for (int64_t i = 0; i < n; ++i) {
         const uint8_t *slot = lat->records + (size_t)lat->rec_head * lat->rec_stride;
         isg_status s = copy_record(lat, slot, &out[i]);
+        if (s == ISG_ERR_DEVICE_TIMEOUT) {  // a failed record is dropped
+            lat->rec_head = (lat->rec_head + 1) % lat->rec_cap;
+            lat->rec_count -= 1;
+        }
         if (s != ISG_OK)
             return s;
         lat->rec_head = (lat->rec_head + 1) % lat->rec_cap;

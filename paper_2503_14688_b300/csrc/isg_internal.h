@@ -107,6 +107,12 @@ uint64_t sw_threshold(double beta);
 cudaError_t dev_malloc_raw(void **p, size_t bytes);
 cudaError_t dev_malloc_async_raw(void **p, size_t bytes, cudaStream_t st);
 bool injected_launch_failure();
+// An armed ISG_INJECT_WAIT: the k-th streamed record pass under-delivers the
+// bytes it announces in one block, so that its bounded waits run out.
+bool injected_wait_failure();
+// Sweep field of a record whose pass gave up waiting (a bounded wait ran
+// out); the host reports ISG_ERR_DEVICE_TIMEOUT when it reads one.
+constexpr int64_t kRecordFailed = INT64_MIN;
 template <class T>
 cudaError_t dev_malloc(T **p, size_t bytes)
 {

@@ -22,6 +22,7 @@
 
 #include <cstdint>
 
+#include "isg_bulk.cuh"
 #include "isg_internal.h"
 #include "isg_philox.cuh"
 #include "isg_sweep_core.cuh"
@@ -110,15 +111,6 @@ __device__ __forceinline__ Words<V> side_words(const Words<V> &S, uint32_t edge,
             X.v[v] = (S.v[v] >> 1) | ((v < V - 1 ? S.v[v + 1] : edge) << 31);
     }
     return X;
-}
-
-// Index of the word adjacent to the V-word group starting at w0 on the side
-// that parity needs, with periodic wrap.
-__device__ __forceinline__ int64_t edge_word(int64_t w0, int V, int64_t W, int parity)
-{
-    if (parity == 0)
-        return w0 == 0 ? W - 1 : w0 - 1;
-    return w0 + V == W ? 0 : w0 + V;
 }
 
 // ---------------------------------------------------------------------------
@@ -455,6 +447,138 @@ __device__ __forceinline__ void cc_zero(ColumnCounter &k)
         k.high[l] = 0;
 }
 
+// The running state of one thread's walk down its word column: the
+// accumulators, the colour-0 rows above (U) and beside (S) the current
+// colour-1 row, and the column counters (even / odd columns, +1 and, for
+// Blume-Capel, -1 sites).
+struct MeasureState {
+    int accB, accM, accQ;
+    uint32_t Up, Sp, Un, Sn;
+    ColumnCounter ce_p, co_p, ce_m, co_m;
+};
+
+template <int MODEL>
+__device__ __forceinline__ void measure_init(MeasureState &m)
+{
+    m.accB = m.accM = m.accQ = 0;
+    m.Up = m.Sp = m.Un = m.Sn = 0;
+    cc_zero(m.ce_p);
+    cc_zero(m.co_p);
+    if (MODEL == 1) {
+        cc_zero(m.ce_m);
+        cc_zero(m.co_m);
+    }
+}
+
+// Row values in raw form: a thread's part of a row sum is, for Ising,
+// 2 raw - 64 with raw = the +1 sites among its 64 (raw = 32 for a lane with
+// no column), and for Blume-Capel raw - 64 with raw = 64 + (+1 sites) -
+// (-1 sites) (64 for a lane with no column): always in [0, 128], so that
+// two rows' warp sums fit the 16-bit halves of one word.
+template <int MODEL>
+__device__ __forceinline__ int raw_to_row(int raw_sum, int lanes)
+{
+    return MODEL == 0 ? 2 * raw_sum - 64 * lanes : raw_sum - 64 * lanes;
+}
+
+// One group of four rows (row r has parity r & 1): per row the colour-1
+// target words Tp (Tn), the colour-0 row below Dp (Dn) and the colour-0
+// side word Ep (En) of the row itself.  Bonds, magnetisation (raw) and
+// occupancy go to the accumulators, each row's raw value to raw[r] for the
+// caller's row reduction, and the column counters advance (g = the group's
+// index within its 16-row block).
+template <int MODEL>
+__device__ __forceinline__ void measure_group(MeasureState &m, const uint32_t (&Tp)[4],
+                                              const uint32_t (&Dp)[4], const uint32_t (&Ep)[4],
+                                              const uint32_t (&Tn)[4], const uint32_t (&Dn)[4],
+                                              const uint32_t (&En)[4], bool active, int (&raw)[4], int g)
+{
+    uint32_t evp[4], odp[4], evm[4], odm[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const bool odd = r & 1;
+        const uint32_t Xp = odd ? (m.Sp << 1) | (Ep[r] >> 31) : (m.Sp >> 1) | (Ep[r] << 31);
+        if (MODEL == 0) {
+            const uint32_t T = Tp[r];
+            const int anti = __popc(T ^ m.Up) + __popc(T ^ Dp[r]) + __popc(T ^ m.Sp) + __popc(T ^ Xp);
+            m.accB += 128 - 2 * anti;
+            raw[r] = active ? __popc(T) + __popc(m.Sp) : 32;
+            evp[r] = odd ? T : m.Sp;
+            odp[r] = odd ? m.Sp : T;
+        } else {
+            const uint32_t Xn = odd ? (m.Sn << 1) | (En[r] >> 31) : (m.Sn >> 1) | (En[r] << 31);
+            const uint32_t Tn_ = Tn[r], Tp_ = Tp[r];
+            const uint32_t nb[4] = {m.Un, Dn[r], m.Sn, Xn}, pb[4] = {m.Up, Dp[r], m.Sp, Xp};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const uint32_t both = Tn_ & nb[k];
+                m.accB += __popc(both) - 2 * __popc(both & (Tp_ ^ pb[k]));
+            }
+            const uint32_t plus1 = Tn_ & Tp_, minus1 = Tn_ & ~Tp_;
+            const uint32_t plus0 = m.Sn & m.Sp, minus0 = m.Sn & ~m.Sp;
+            // (+1) - (-1) = 2 (+1) - (occupied); the occupied count is Q's
+            const int occ = __popc(Tn_) + __popc(m.Sn);
+            m.accQ += occ;
+            raw[r] = active ? 64 + 2 * (__popc(plus1) + __popc(plus0)) - occ : 64;
+            evp[r] = odd ? plus1 : plus0;
+            odp[r] = odd ? plus0 : plus1;
+            evm[r] = odd ? minus1 : minus0;
+            odm[r] = odd ? minus0 : minus1;
+            m.Un = m.Sn;
+            m.Sn = Dn[r];
+        }
+        m.accM += raw[r];
+        m.Up = m.Sp;
+        m.Sp = Dp[r];
+    }
+    cc_add4(m.ce_p, evp[0], evp[1], evp[2], evp[3], g);
+    cc_add4(m.co_p, odp[0], odp[1], odp[2], odp[3], g);
+    if (MODEL == 1) {
+        cc_add4(m.ce_m, evm[0], evm[1], evm[2], evm[3], g);
+        cc_add4(m.co_m, odm[0], odm[1], odm[2], odm[3], g);
+    }
+}
+
+// End of a band of `rows` rows: B, M, Q summed per warp into the record
+// header, and every column's count (one site per row of the band) added to
+// C.  Every lane of the warp takes part.
+template <int MODEL>
+__device__ __forceinline__ void measure_finish(MeasureState &m, bool active, int rows, int64_t wc,
+                                               int64_t *__restrict__ rec_hdr, int32_t *__restrict__ C)
+{
+    m.accM = raw_to_row<MODEL>(m.accM, rows);  // raw over the band's rows -> its part of M
+    if (!active)
+        m.accB = m.accM = m.accQ = 0;
+    if (MODEL == 0)
+        m.accQ = active ? 64 * rows : 0;
+    const int accB = __reduce_add_sync(0xFFFFFFFFu, m.accB);
+    const int accM = __reduce_add_sync(0xFFFFFFFFu, m.accM);
+    const int accQ = __reduce_add_sync(0xFFFFFFFFu, m.accQ);
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 1), (unsigned long long)(int64_t)accB);
+        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 2), (unsigned long long)(int64_t)accM);
+        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 3), (unsigned long long)(int64_t)accQ);
+    }
+    if (active) {
+#pragma unroll 4
+        for (int b = 0; b < 32; ++b) {
+            const int64_t xe = 2 * (32 * wc + b);
+            int ve, vo;
+            if (MODEL == 0) {
+                ve = 2 * cc_get(m.ce_p, b) - rows;
+                vo = 2 * cc_get(m.co_p, b) - rows;
+            } else {
+                ve = cc_get(m.ce_p, b) - cc_get(m.ce_m, b);
+                vo = cc_get(m.co_p, b) - cc_get(m.co_m, b);
+            }
+            if (ve)
+                atomicAdd(&C[xe], ve);
+            if (vo)
+                atomicAdd(&C[xe + 1], vo);
+        }
+    }
+}
+
 // base: row 0 of plane 0; L rows of W words per plane, planes LW words
 // apart.  kWrap = true: the periodic lattice (L rows).  kWrap = false: a row
 // slab whose planes have a halo row above row 0 and below row L - 1, which
@@ -482,22 +606,15 @@ __device__ __forceinline__ void measure_band(const uint32_t *base, int64_t L, in
     const uint32_t *n0 = base, *n1 = base + 2 * LW;  // Blume-Capel only
     const int64_t wl = wc == 0 ? W - 1 : wc - 1, wr = wc + 1 == W ? 0 : wc + 1;
 
-    int accB = 0, accM = 0, accQ = 0;
-    ColumnCounter ce_p, co_p, ce_m, co_m;  // even/odd columns, +1 / -1 sites
-    cc_zero(ce_p);
-    cc_zero(co_p);
-    if (MODEL == 1) {
-        cc_zero(ce_m);
-        cc_zero(co_m);
-    }
+    MeasureState m;
+    measure_init<MODEL>(m);
     const int64_t yup = (kWrap && y0 == 0) ? L - 1 : y0 - 1;
-    uint32_t Up = 0, Sp = 0, Un = 0, Sn = 0;
     if (active) {
-        Up = __ldg(p0 + yup * W + wc);
-        Sp = __ldg(p0 + y0 * W + wc);
+        m.Up = __ldg(p0 + yup * W + wc);
+        m.Sp = __ldg(p0 + y0 * W + wc);
         if (MODEL == 1) {
-            Un = __ldg(n0 + yup * W + wc);
-            Sn = __ldg(n0 + y0 * W + wc);
+            m.Un = __ldg(n0 + yup * W + wc);
+            m.Sn = __ldg(n0 + y0 * W + wc);
         }
     }
     // Bands start at multiples of 16 rows and groups at multiples of 4, so row
@@ -539,55 +656,13 @@ __device__ __forceinline__ void measure_band(const uint32_t *base, int64_t L, in
         }
     };
     auto process = [&](const Group &G, int gg) {
-        uint32_t evp[4], odp[4], evm[4], odm[4];
+        int raw[4];
+        measure_group<MODEL>(m, G.Tp, G.Dp, G.Ep, G.Tn, G.Dn, G.En, active, raw, gg & 3);
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            const bool odd = r & 1;
-            const uint32_t Xp = odd ? (Sp << 1) | (G.Ep[r] >> 31) : (Sp >> 1) | (G.Ep[r] << 31);
-            int rowpart;
-            if (MODEL == 0) {
-                const uint32_t T = G.Tp[r];
-                const int anti = __popc(T ^ Up) + __popc(T ^ G.Dp[r]) + __popc(T ^ Sp) +
-                                 __popc(T ^ Xp);
-                accB += 128 - 2 * anti;
-                rowpart = 2 * (__popc(T) + __popc(Sp)) - 64;
-                evp[r] = odd ? T : Sp;
-                odp[r] = odd ? Sp : T;
-            } else {
-                const uint32_t Xn = odd ? (Sn << 1) | (G.En[r] >> 31) : (Sn >> 1) | (G.En[r] << 31);
-                const uint32_t Tn_ = G.Tn[r], Tp_ = G.Tp[r];
-                const uint32_t nb[4] = {Un, G.Dn[r], Sn, Xn}, pb[4] = {Up, G.Dp[r], Sp, Xp};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    const uint32_t both = Tn_ & nb[k];
-                    accB += __popc(both) - 2 * __popc(both & (Tp_ ^ pb[k]));
-                }
-                const uint32_t plus1 = Tn_ & Tp_, minus1 = Tn_ & ~Tp_;
-                const uint32_t plus0 = Sn & Sp, minus0 = Sn & ~Sp;
-                rowpart = __popc(plus1) + __popc(plus0) - __popc(minus1) - __popc(minus0);
-                accQ += __popc(Tn_) + __popc(Sn);
-                evp[r] = odd ? plus1 : plus0;
-                odp[r] = odd ? plus0 : plus1;
-                evm[r] = odd ? minus1 : minus0;
-                odm[r] = odd ? minus0 : minus1;
-                Un = Sn;
-                Sn = G.Dn[r];
-            }
-            if (!active)
-                rowpart = 0;
-            accM += rowpart;
-            const int rs = __reduce_add_sync(0xFFFFFFFFu, rowpart);
+            const int rs = __reduce_add_sync(0xFFFFFFFFu, raw[r]);
             if ((threadIdx.x & 31) == 0)
-                atomicAdd(&s_row[4 * gg + r], rs);
-            Up = Sp;
-            Sp = G.Dp[r];
-        }
-        const int g = gg & 3;  // group within its 16-row block
-        cc_add4(ce_p, evp[0], evp[1], evp[2], evp[3], g);
-        cc_add4(co_p, odp[0], odp[1], odp[2], odp[3], g);
-        if (MODEL == 1) {
-            cc_add4(ce_m, evm[0], evm[1], evm[2], evm[3], g);
-            cc_add4(co_m, odm[0], odm[1], odm[2], odm[3], g);
+                atomicAdd(&s_row[4 * gg + r], raw_to_row<MODEL>(rs, 32));
         }
     };
     Group A, B;
@@ -610,37 +685,7 @@ __device__ __forceinline__ void measure_band(const uint32_t *base, int64_t L, in
             process(A, gg);
         }
     }
-    if (!active)
-        accB = accQ = 0;
-    if (MODEL == 0)
-        accQ = active ? 64 * rows : 0;
-    accB = __reduce_add_sync(0xFFFFFFFFu, accB);
-    accM = __reduce_add_sync(0xFFFFFFFFu, accM);
-    accQ = __reduce_add_sync(0xFFFFFFFFu, accQ);
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 1), (unsigned long long)(int64_t)accB);
-        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 2), (unsigned long long)(int64_t)accM);
-        atomicAdd(reinterpret_cast<unsigned long long *>(rec_hdr + 3), (unsigned long long)(int64_t)accQ);
-    }
-    if (active) {
-        // every column gets one site per row of the band
-#pragma unroll 4
-        for (int b = 0; b < 32; ++b) {
-            const int64_t xe = 2 * (32 * wc + b);
-            int ve, vo;
-            if (MODEL == 0) {
-                ve = 2 * cc_get(ce_p, b) - rows;
-                vo = 2 * cc_get(co_p, b) - rows;
-            } else {
-                ve = cc_get(ce_p, b) - cc_get(ce_m, b);
-                vo = cc_get(co_p, b) - cc_get(co_m, b);
-            }
-            if (ve)
-                atomicAdd(&C[xe], ve);
-            if (vo)
-                atomicAdd(&C[xe + 1], vo);
-        }
-    }
+    measure_finish<MODEL>(m, active, rows, wc, rec_hdr, C);
     __syncthreads();
     for (int i = threadIdx.x; i < rows; i += blockDim.x)
         if (s_row[i])
@@ -654,6 +699,226 @@ __global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? kMeasureBlocksIs
 {
     __shared__ int32_t s_row[kMeasureBand];
     measure_band<MODEL>(pl.base, pl.L, pl.W, pl.L * pl.W, H, rec_hdr, R, C, sweep, s_row);
+}
+
+// ---------------------------------------------------------------------------
+// The record pass with its rows streamed into shared memory by the copy
+// engine (k_measure_stream): the walk and arithmetic of k_measure
+// (measure_group / measure_finish), for lattices whose rows split into whole
+// segments of kStreamSeg words (L a multiple of 16384).  A block has one
+// consumer thread per word of its segment (8 warps) and one producer warp,
+// whose lane 0 copies 4-row groups into a ring of shared-memory stages with
+// 1D bulk copies that complete on the stage's `full` mbarrier.  Consumer
+// warps release a stage through its `empty` mbarrier, and the producer then
+// adds that group's row sums to R before it refills the stage: each warp
+// leaves the warp sums of the group's four raw row values, two rows to a
+// word (16-bit halves), in shared memory.  Per row a stage holds the colour-1 target segment and
+// the colour-0 row below it with kStreamHalo words on each side: the side
+// neighbours of the segment's edge words, taken from the row's other end at
+// the periodic wrap.  Every wait is bounded (kStreamWaitNs); one that runs
+// out marks the record failed (sweep field INT64_MIN, read by the host as
+// ISG_ERR_DEVICE_TIMEOUT), and the producer waits (bounded) for its copies
+// in flight before the block returns.
+// ---------------------------------------------------------------------------
+constexpr int kStreamSeg = 256;   // words per segment: one consumer thread each
+constexpr int kStreamHalo = 4;    // 16 bytes, the bulk-copy granule
+constexpr int kStreamRowD = kStreamSeg + 2 * kStreamHalo;
+constexpr int kStreamThreads = kStreamSeg + 32;
+constexpr uint64_t kStreamWaitNs = 2000000000ull;
+
+template <int MODEL>
+struct StreamShape {
+    static constexpr int kPlanes = MODEL == 0 ? 1 : 2;   // sign (and occupancy) planes per colour
+    static constexpr int kStages = MODEL == 0 ? 8 : 4;
+    static constexpr int kRowWords = kPlanes * (kStreamSeg + kStreamRowD);
+    static constexpr int kStageWords = 4 * kRowWords;
+    static constexpr uint32_t kStageBytes = 4u * kStageWords;
+    // stages, then kStages full and kStages empty barriers, then per stage and
+    // consumer warp its two packed row-pair sums
+    static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 16 * kStages + 64 * kStages;
+    // word offsets in a stage: colour-1 plane q of row r; colour-0 plane q
+    // of the row below row r (halo words included)
+    static __device__ __forceinline__ int t_off(int r, int q) { return r * kRowWords + q * kStreamSeg; }
+    static __device__ __forceinline__ int d_off(int r, int q)
+    {
+        return r * kRowWords + kPlanes * kStreamSeg + q * kStreamRowD;
+    }
+};
+
+__device__ __forceinline__ void mark_record_failed(int64_t *rec_hdr)
+{
+    atomicExch(reinterpret_cast<unsigned long long *>(rec_hdr), (unsigned long long)INT64_MIN);
+}
+
+// The producer (one thread): copies of group gg go to stage gg % kStages;
+// c0[q] / c1[q]: colour-0 / colour-1 plane q (0: sign, 1: occupancy).
+// tx_extra (0 except under ISG_INJECT_WAIT): bytes announced for the first
+// group on top of those copied, so that its waits run out.
+template <int MODEL>
+__device__ void stream_produce(uint32_t sbase, uint32_t full0, uint32_t empty0, const uint32_t *s_part,
+                               const uint32_t *const (&c0)[2], const uint32_t *const (&c1)[2], int64_t L,
+                               int64_t W, int64_t y0, int64_t seg0, int ngroups, int32_t *__restrict__ R,
+                               int64_t *rec_hdr, uint32_t tx_extra)
+{
+    using S = StreamShape<MODEL>;
+    const bool inner = seg0 >= kStreamHalo && seg0 + kStreamSeg + kStreamHalo <= W;
+    const int64_t left = seg0 >= kStreamHalo ? seg0 - kStreamHalo : W - kStreamHalo;
+    const int64_t right = seg0 + kStreamSeg < W ? seg0 + kStreamSeg : 0;
+    int issued = 0;
+    bool ok = true;
+    for (int gg = 0; gg < ngroups + S::kStages; ++gg) {
+        const int s = gg % S::kStages;
+        if (gg >= S::kStages) {
+            const int done = gg - S::kStages;  // the group the consumers release from stage s
+            if (done >= ngroups)
+                break;
+            if (!mbar_wait(empty0 + 8u * s, (uint32_t)((done / S::kStages) & 1), kStreamWaitNs)) {
+                ok = false;
+                break;
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                uint32_t tot = 0;  // halves stay below 2^16: 8 warps x 32 lanes x 128
+#pragma unroll
+                for (int w = 0; w < kStreamSeg / 32; ++w)
+                    tot += s_part[2 * (s * (kStreamSeg / 32) + w) + h];
+                const int64_t y = y0 + 4 * done + 2 * h;
+                const int v0 = raw_to_row<MODEL>((int)(tot & 0xFFFFu), kStreamSeg);
+                const int v1 = raw_to_row<MODEL>((int)(tot >> 16), kStreamSeg);
+                if (v0)
+                    atomicAdd(&R[y], v0);
+                if (v1)
+                    atomicAdd(&R[y + 1], v1);
+            }
+        }
+        if (gg < ngroups) {
+            const uint32_t full = full0 + 8u * s;
+            const uint32_t st = sbase + (uint32_t)s * S::kStageBytes;
+            mbar_expect_tx(full, S::kStageBytes + (gg == 0 ? tx_extra : 0u));
+#pragma unroll 1
+            for (int r = 0; r < 4; ++r) {
+                const int64_t y = y0 + 4 * gg + r, yd = y + 1 == L ? 0 : y + 1;
+#pragma unroll
+                for (int q = 0; q < S::kPlanes; ++q) {
+                    bulk_load(st + 4u * S::t_off(r, q), c1[q] + y * W + seg0, 4u * kStreamSeg, full);
+                    const uint32_t d = st + 4u * S::d_off(r, q);
+                    const uint32_t *row = c0[q] + yd * W;
+                    if (inner) {
+                        bulk_load(d, row + seg0 - kStreamHalo, 4u * kStreamRowD, full);
+                    } else {
+                        bulk_load(d, row + left, 4u * kStreamHalo, full);
+                        bulk_load(d + 4u * kStreamHalo, row + seg0, 4u * kStreamSeg, full);
+                        bulk_load(d + 4u * (kStreamHalo + kStreamSeg), row + right, 4u * kStreamHalo, full);
+                    }
+                }
+            }
+            issued = gg + 1;
+        }
+    }
+    if (!ok) {
+        mark_record_failed(rec_hdr);
+        // the latest group issued into each stage must have landed before
+        // the block's shared memory goes away
+        for (int s = 0; s < S::kStages && s < issued; ++s) {
+            const int last = s + S::kStages * ((issued - 1 - s) / S::kStages);
+            mbar_wait(full0 + 8u * s, (uint32_t)((last / S::kStages) & 1), kStreamWaitNs);
+        }
+    }
+}
+
+template <int MODEL>
+__global__ void __launch_bounds__(kStreamThreads, MODEL == 0 ? 3 : 2)
+    k_measure_stream(Planes pl, int H, int64_t *__restrict__ rec_hdr, int32_t *__restrict__ R,
+                     int32_t *__restrict__ C, int64_t sweep, uint32_t tx_extra)
+{
+    using S = StreamShape<MODEL>;
+    extern __shared__ __align__(128) uint32_t smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + S::kStages * S::kStageWords);
+    uint32_t *s_part = reinterpret_cast<uint32_t *>(bars + 2 * S::kStages);
+    const uint32_t full0 = smem_u32(bars), empty0 = smem_u32(bars + S::kStages);
+    const int64_t L = pl.L, W = pl.W, LW = L * W;
+    const int64_t y0 = (int64_t)blockIdx.y * H;
+    const int rows = (int)((y0 + H < L ? y0 + H : L) - y0);  // a multiple of 16
+    const int ngroups = rows / 4;
+    const int64_t seg0 = (int64_t)blockIdx.x * kStreamSeg;
+    const uint32_t *const c0[2] = {MODEL == 0 ? pl.base : pl.base + LW, pl.base};
+    const uint32_t *const c1[2] = {MODEL == 0 ? pl.base + LW : pl.base + 3 * LW, pl.base + 2 * LW};
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S::kStages; ++s) {
+            mbar_init(full0 + 8u * s, 1);
+            mbar_init(empty0 + 8u * s, kStreamSeg / 32);
+        }
+        mbar_fence_init();
+        if (blockIdx.x == 0 && blockIdx.y == 0)  // the slot is zeroed; a failure mark stays
+            atomicCAS(reinterpret_cast<unsigned long long *>(rec_hdr), 0ull, (unsigned long long)sweep);
+    }
+    __syncthreads();
+    if (threadIdx.x >= kStreamSeg) {
+        if (threadIdx.x == kStreamSeg)
+            stream_produce<MODEL>(smem_u32(smem), full0, empty0, s_part, c0, c1, L, W, y0, seg0, ngroups, R,
+                                  rec_hdr, blockIdx.x == 0 && blockIdx.y == 0 ? tx_extra : 0u);
+        return;
+    }
+    const int t = threadIdx.x;
+    const int64_t wc = seg0 + t;
+    const int64_t wr = wc + 1 == W ? 0 : wc + 1;
+    const int64_t yup = y0 == 0 ? L - 1 : y0 - 1;
+    MeasureState m;
+    measure_init<MODEL>(m);
+    m.Up = __ldg(c0[0] + yup * W + wc);
+    m.Sp = __ldg(c0[0] + y0 * W + wc);
+    // side word of the next group's first row (even: to the right)
+    uint32_t Ecp = __ldg(c0[0] + y0 * W + wr), Ecn = 0;
+    if (MODEL == 1) {
+        m.Un = __ldg(c0[1] + yup * W + wc);
+        m.Sn = __ldg(c0[1] + y0 * W + wc);
+        Ecn = __ldg(c0[1] + y0 * W + wr);
+    }
+    const int warp = t >> 5, lane = t & 31;
+    // 16 rows (four groups, one 16-row block of the column counters) per
+    // iteration: a band has a multiple of 16 rows, and kStages is a
+    // multiple of 4, so the four groups take consecutive stages of one phase
+#pragma unroll 1
+    for (int gb = 0; gb < ngroups; gb += 4) {
+        const uint32_t parity = (uint32_t)((gb / S::kStages) & 1);
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int s = gb % S::kStages + g;
+            if (!mbar_wait(full0 + 8u * s, parity, kStreamWaitNs)) {
+                mark_record_failed(rec_hdr);
+                return;
+            }
+            const uint32_t *st = smem + s * S::kStageWords;
+            uint32_t Tp[4], Dp[4], Ep[4], Tn[4], Dn[4], En[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                Tp[r] = st[S::t_off(r, 0) + t];
+                Dp[r] = st[S::d_off(r, 0) + kStreamHalo + t];
+                // the row's own colour-0 words are the previous row's "below"
+                Ep[r] = r == 0 ? Ecp : st[S::d_off(r - 1, 0) + kStreamHalo + t + ((r & 1) ? -1 : 1)];
+                if (MODEL == 1) {
+                    Tn[r] = st[S::t_off(r, 1) + t];
+                    Dn[r] = st[S::d_off(r, 1) + kStreamHalo + t];
+                    En[r] = r == 0 ? Ecn : st[S::d_off(r - 1, 1) + kStreamHalo + t + ((r & 1) ? -1 : 1)];
+                } else {
+                    Tn[r] = Dn[r] = En[r] = 0;
+                }
+            }
+            Ecp = st[S::d_off(3, 0) + kStreamHalo + t + 1];
+            if (MODEL == 1)
+                Ecn = st[S::d_off(3, 1) + kStreamHalo + t + 1];
+            int raw[4];
+            measure_group<MODEL>(m, Tp, Dp, Ep, Tn, Dn, En, true, raw, g);
+            const uint32_t p01 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)raw[0] | ((uint32_t)raw[1] << 16));
+            const uint32_t p23 = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)raw[2] | ((uint32_t)raw[3] << 16));
+            if (lane == 0) {
+                *reinterpret_cast<uint2 *>(s_part + 2 * (s * (kStreamSeg / 32) + warp)) = make_uint2(p01, p23);
+                mbar_arrive(empty0 + 8u * s);
+            }
+            __syncwarp();
+        }
+    }
+    measure_finish<MODEL>(m, true, rows, wc, rec_hdr, C);
 }
 
 // Records of many lattices of one side L in one launch (the ensemble's
@@ -1184,6 +1449,26 @@ cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaSt
     while (H % 32 == 0 && bx * ((pl.L + H - 1) / H) < 148 * 4)
         H >>= 1;
     const dim3 grid((unsigned)bx, (unsigned)((pl.L + H - 1) / H));
+    if (pl.W % kStreamSeg == 0 && (reinterpret_cast<uintptr_t>(pl.base) & 15u) == 0) {
+        // whole segments (and the 16-byte aligned planes bulk copies need):
+        // the streamed pass, on the same grid, one segment per block
+        const uint32_t extra = injected_wait_failure() ? 16u : 0u;
+        cudaError_t e;
+        if (pl.model == 0) {
+            e = cudaFuncSetAttribute(k_measure_stream<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)StreamShape<0>::kSmem);
+            if (e == cudaSuccess)
+                k_measure_stream<0><<<grid, kStreamThreads, StreamShape<0>::kSmem, st>>>(pl, (int)H, hdr, R, C,
+                                                                                      sweep, extra);
+        } else {
+            e = cudaFuncSetAttribute(k_measure_stream<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)StreamShape<1>::kSmem);
+            if (e == cudaSuccess)
+                k_measure_stream<1><<<grid, kStreamThreads, StreamShape<1>::kSmem, st>>>(pl, (int)H, hdr, R, C,
+                                                                                      sweep, extra);
+        }
+        return e != cudaSuccess ? e : cudaGetLastError();
+    }
     if (pl.model == 0)
         k_measure<0><<<grid, kMeasureThreads, 0, st>>>(pl, (int)H, hdr, R, C, sweep);
     else

@@ -125,6 +125,9 @@ extern "C" isg_status isg_measure_planes_noalloc(int32_t model, int64_t L, const
         return isg::report_error(ISG_ERR_CUDA, "isg_measure_planes_noalloc: %s",
                                  cudaGetErrorString(e));
     }
+    if (hdr[0] == isg::kRecordFailed)
+        return isg::report_error(ISG_ERR_DEVICE_TIMEOUT,
+                                 "isg_measure_planes_noalloc: the record pass ran out of time");
     out->sweep = hdr[0];
     out->B = hdr[1];
     out->M = hdr[2];

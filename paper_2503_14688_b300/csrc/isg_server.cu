@@ -259,6 +259,11 @@ isg_status run_round(isg_server *s)
     for (size_t i = 0; i < s->active.size();) {
         Request &r = *s->reqs[s->active[i]];
         if (r.finish_queued && cudaEventQuery(r.done) == cudaSuccess) {
+            if (s->h_finals[4 * r.final_slot] == kRecordFailed) {
+                // the final record pass ran out of time: the request fails
+                drop(s, r, ISG_REQ_FAILED, ISG_ERR_DEVICE_TIMEOUT);
+                continue;
+            }
             float ms = 0;
             cudaEventElapsedTime(&ms, s->ev0, r.done);
             r.t_done = 1e-3 * ms;
@@ -705,6 +710,11 @@ isg_status isg_server_read_records(isg_server *s, uint64_t id, isg_obs *out, int
         const uint8_t *slot = r.recs + stride * (size_t)(r.rec_read + i);
         int64_t hdr[4];
         SCUDA(cudaMemcpy(hdr, slot, sizeof(hdr), cudaMemcpyDeviceToHost), "record read");
+        if (hdr[0] == kRecordFailed) {
+            r.rec_read += i + 1;  // dropped
+            return sfail(ISG_ERR_DEVICE_TIMEOUT, "record %lld of request %llu: its pass ran out of time",
+                         (long long)(r.rec_read - 1), (unsigned long long)id);
+        }
         out[i].sweep = hdr[0];
         out[i].B = hdr[1];
         out[i].M = hdr[2];

@@ -262,5 +262,7 @@ def xi_integral(r, c, r_cut: float) -> float:
 def inject_fault(what: int, after: int):
     """isg_debug_inject: the after-th device allocation (what =
     ISG_INJECT_ALLOC) or sweep launch (ISG_INJECT_LAUNCH) from now on fails,
-    once; after = 0 disarms.  For testing error paths on the host."""
+    or the after-th streamed record pass runs out its bounded waits
+    (ISG_INJECT_WAIT); once; after = 0 disarms.  For testing error paths
+    without a device fault."""
     check(lib().isg_debug_inject(int(what), int(after)))
