@@ -1,6 +1,7 @@
-// isg_bulk.cuh -- shared-memory barriers (mbarrier) and 1D bulk copies
-// (cp.async.bulk, the copy engine's untiled form) as inline PTX, for
-// kernels that stream rows of a plane into shared memory.
+// isg_bulk.cuh -- shared-memory barriers (mbarrier), 1D bulk copies
+// (cp.async.bulk, the copy engine's untiled form) and tiled tensor copies
+// (cp.async.bulk.tensor) as inline PTX, for kernels that stream rows of a
+// plane into shared memory.
 //
 // A bulk copy moves `bytes` (a multiple of 16) from a 16-byte aligned
 // global address to a 16-byte aligned shared address and reports its bytes
@@ -83,6 +84,19 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void *src, uint32_
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
         "l"(src), "r"(bytes), "r"(bar)
+        : "memory");
+}
+
+// Tiled copy of one box of a 3D tensor map (a __grid_constant__ kernel
+// parameter) at element coordinates (x, y, z) into shared memory (128-byte
+// aligned), reporting its bytes to `bar`.  x times the element size must be
+// a multiple of 16 bytes.
+__device__ __forceinline__ void tensor_load_3d(uint32_t dst, const void *tmap, int x, int y, int z, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
 }
 

@@ -18,6 +18,8 @@
 // Every kernel is integer-only: no tensor cores, nothing here is a
 // contraction.  The sweep kernels are bound by the integer issue rate of the
 // Philox evaluations (one per four sites) and the threshold compares.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -707,8 +709,10 @@ __global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? kMeasureBlocksIs
 // (measure_group / measure_finish), for lattices whose rows split into whole
 // segments of kStreamSeg words (L a multiple of 16384).  A block has one
 // consumer thread per word of its segment (8 warps) and one producer warp,
-// whose lane 0 copies 4-row groups into a ring of shared-memory stages with
-// 1D bulk copies that complete on the stage's `full` mbarrier.  Consumer
+// whose lane 0 copies 4-row groups into a ring of shared-memory stages,
+// completing on the stage's `full` mbarrier: per plane one tiled copy of a
+// 4-row box through a tensor map of the planes (away from the row ends and
+// the periodic wrap), else one 1D bulk copy per row.  Consumer
 // warps release a stage through its `empty` mbarrier, and the producer then
 // adds that group's row sums to R before it refills the stage: each warp
 // leaves the warp sums of the group's four raw row values, two rows to a
@@ -730,18 +734,20 @@ template <int MODEL>
 struct StreamShape {
     static constexpr int kPlanes = MODEL == 0 ? 1 : 2;   // sign (and occupancy) planes per colour
     static constexpr int kStages = MODEL == 0 ? 8 : 4;
-    static constexpr int kRowWords = kPlanes * (kStreamSeg + kStreamRowD);
-    static constexpr int kStageWords = 4 * kRowWords;
+    // per plane: the 4 colour-1 rows, then the 4 colour-0 rows below them
+    // (the layouts of the two tiled boxes; every block 128-byte aligned)
+    static constexpr int kPlaneWords = 4 * (kStreamSeg + kStreamRowD);
+    static constexpr int kStageWords = kPlanes * kPlaneWords;
     static constexpr uint32_t kStageBytes = 4u * kStageWords;
     // stages, then kStages full and kStages empty barriers, then per stage and
     // consumer warp its two packed row-pair sums
     static constexpr size_t kSmem = (size_t)kStages * kStageBytes + 16 * kStages + 64 * kStages;
     // word offsets in a stage: colour-1 plane q of row r; colour-0 plane q
     // of the row below row r (halo words included)
-    static __device__ __forceinline__ int t_off(int r, int q) { return r * kRowWords + q * kStreamSeg; }
+    static __device__ __forceinline__ int t_off(int r, int q) { return q * kPlaneWords + r * kStreamSeg; }
     static __device__ __forceinline__ int d_off(int r, int q)
     {
-        return r * kRowWords + kPlanes * kStreamSeg + q * kStreamRowD;
+        return q * kPlaneWords + 4 * kStreamSeg + r * kStreamRowD;
     }
 };
 
@@ -752,15 +758,21 @@ __device__ __forceinline__ void mark_record_failed(int64_t *rec_hdr)
 
 // The producer (one thread): copies of group gg go to stage gg % kStages;
 // c0[q] / c1[q]: colour-0 / colour-1 plane q (0: sign, 1: occupancy).
-// tx_extra (0 except under ISG_INJECT_WAIT): bytes announced for the first
-// group on top of those copied, so that its waits run out.
+// tmT / tmD (used when tmap): tensor maps of all planes as (W / 2) x L x
+// planes 8-byte elements with boxes of 128 x 4 x 1 (colour-1 rows) and
+// 132 x 4 x 1 (colour-0 rows with halos).  tx_extra (0 except under
+// ISG_INJECT_WAIT): bytes announced for the first group on top of those
+// copied, so that its waits run out.
 template <int MODEL>
 __device__ void stream_produce(uint32_t sbase, uint32_t full0, uint32_t empty0, const uint32_t *s_part,
                                const uint32_t *const (&c0)[2], const uint32_t *const (&c1)[2], int64_t L,
                                int64_t W, int64_t y0, int64_t seg0, int ngroups, int32_t *__restrict__ R,
-                               int64_t *rec_hdr, uint32_t tx_extra)
+                               int64_t *rec_hdr, uint32_t tx_extra, const CUtensorMap *tmT,
+                               const CUtensorMap *tmD, bool tmap)
 {
     using S = StreamShape<MODEL>;
+    // plane index in the tensor maps: colour-0 / colour-1 sign (and occupancy)
+    const int z0[2] = {MODEL == 0 ? 0 : 1, 0}, z1[2] = {MODEL == 0 ? 1 : 3, 2};
     const bool inner = seg0 >= kStreamHalo && seg0 + kStreamSeg + kStreamHalo <= W;
     const int64_t left = seg0 >= kStreamHalo ? seg0 - kStreamHalo : W - kStreamHalo;
     const int64_t right = seg0 + kStreamSeg < W ? seg0 + kStreamSeg : 0;
@@ -795,6 +807,17 @@ __device__ void stream_produce(uint32_t sbase, uint32_t full0, uint32_t empty0, 
             const uint32_t full = full0 + 8u * s;
             const uint32_t st = sbase + (uint32_t)s * S::kStageBytes;
             mbar_expect_tx(full, S::kStageBytes + (gg == 0 ? tx_extra : 0u));
+            const int64_t yg = y0 + 4 * gg;
+            if (tmap && inner && yg + 4 < L) {
+#pragma unroll
+                for (int q = 0; q < S::kPlanes; ++q) {
+                    tensor_load_3d(st + 4u * S::t_off(0, q), tmT, (int)(seg0 / 2), (int)yg, z1[q], full);
+                    tensor_load_3d(st + 4u * S::d_off(0, q), tmD, (int)(seg0 / 2) - kStreamHalo / 2, (int)yg + 1,
+                                   z0[q], full);
+                }
+                issued = gg + 1;
+                continue;
+            }
 #pragma unroll 1
             for (int r = 0; r < 4; ++r) {
                 const int64_t y = y0 + 4 * gg + r, yd = y + 1 == L ? 0 : y + 1;
@@ -829,7 +852,8 @@ __device__ void stream_produce(uint32_t sbase, uint32_t full0, uint32_t empty0, 
 template <int MODEL>
 __global__ void __launch_bounds__(kStreamThreads, MODEL == 0 ? 3 : 2)
     k_measure_stream(Planes pl, int H, int64_t *__restrict__ rec_hdr, int32_t *__restrict__ R,
-                     int32_t *__restrict__ C, int64_t sweep, uint32_t tx_extra)
+                     int32_t *__restrict__ C, int64_t sweep, uint32_t tx_extra,
+                     const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmD, int tmap)
 {
     using S = StreamShape<MODEL>;
     extern __shared__ __align__(128) uint32_t smem[];
@@ -856,7 +880,8 @@ __global__ void __launch_bounds__(kStreamThreads, MODEL == 0 ? 3 : 2)
     if (threadIdx.x >= kStreamSeg) {
         if (threadIdx.x == kStreamSeg)
             stream_produce<MODEL>(smem_u32(smem), full0, empty0, s_part, c0, c1, L, W, y0, seg0, ngroups, R,
-                                  rec_hdr, blockIdx.x == 0 && blockIdx.y == 0 ? tx_extra : 0u);
+                                  rec_hdr, blockIdx.x == 0 && blockIdx.y == 0 ? tx_extra : 0u, &tmT, &tmD,
+                                  tmap != 0);
         return;
     }
     const int t = threadIdx.x;
@@ -1436,6 +1461,47 @@ cudaError_t launch_half_sweep_multi(int model, int64_t L, uint32_t *const *plane
     return cudaSuccess;
 }
 
+// The driver's tensor-map encoder, looked up once through the runtime (no
+// link against the driver library); null if this driver lacks it.
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (PFN_cuTensorMapEncodeTiled_v12000) nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// Tensor maps of a lattice's planes for k_measure_stream: (W / 2) x L x
+// planes elements of 8 bytes, boxes of 128 x 4 x 1 (colour-1 rows) and
+// 132 x 4 x 1 (colour-0 rows with 2-element halos).  False if they cannot be
+// made; the pass then copies every row with 1D bulk copies.
+static bool stream_tensor_maps(const Planes &pl, CUtensorMap *tmT, CUtensorMap *tmD)
+{
+    const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc)
+        return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)(pl.W / 2), (cuuint64_t)pl.L, (cuuint64_t)(pl.model == 0 ? 2 : 4)};
+    const cuuint64_t strides[2] = {(cuuint64_t)pl.W * 4, (cuuint64_t)pl.L * (cuuint64_t)pl.W * 4};
+    const cuuint32_t boxT[3] = {kStreamSeg / 2, 4, 1}, boxD[3] = {kStreamRowD / 2, 4, 1}, one[3] = {1, 1, 1};
+    for (int k = 0; k < 2; ++k) {
+        const CUresult r = enc(k == 0 ? tmT : tmD, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, pl.base, dims, strides,
+                               k == 0 ? boxT : boxD, one, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
 cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaStream_t st)
 {
     int64_t *hdr = reinterpret_cast<int64_t *>(record);
@@ -1453,19 +1519,21 @@ cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaSt
         // whole segments (and the 16-byte aligned planes bulk copies need):
         // the streamed pass, on the same grid, one segment per block
         const uint32_t extra = injected_wait_failure() ? 16u : 0u;
+        CUtensorMap tmT, tmD;
+        const int tmap = stream_tensor_maps(pl, &tmT, &tmD) ? 1 : 0;
         cudaError_t e;
         if (pl.model == 0) {
             e = cudaFuncSetAttribute(k_measure_stream<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)StreamShape<0>::kSmem);
             if (e == cudaSuccess)
-                k_measure_stream<0><<<grid, kStreamThreads, StreamShape<0>::kSmem, st>>>(pl, (int)H, hdr, R, C,
-                                                                                      sweep, extra);
+                k_measure_stream<0><<<grid, kStreamThreads, StreamShape<0>::kSmem, st>>>(
+                    pl, (int)H, hdr, R, C, sweep, extra, tmT, tmD, tmap);
         } else {
             e = cudaFuncSetAttribute(k_measure_stream<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)StreamShape<1>::kSmem);
             if (e == cudaSuccess)
-                k_measure_stream<1><<<grid, kStreamThreads, StreamShape<1>::kSmem, st>>>(pl, (int)H, hdr, R, C,
-                                                                                      sweep, extra);
+                k_measure_stream<1><<<grid, kStreamThreads, StreamShape<1>::kSmem, st>>>(
+                    pl, (int)H, hdr, R, C, sweep, extra, tmT, tmD, tmap);
         }
         return e != cudaSuccess ? e : cudaGetLastError();
     }
