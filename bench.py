@@ -96,6 +96,17 @@ def _peaks():
     return 2032.0, "fallback (recipe max SM clock)"
 
 
+def _hbm_peak():
+    """Copy bandwidth in GB/s: the measured one, else the recipe's fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            p = json.load(f)
+        if "hbm_gbs" in p:
+            return float(p["hbm_gbs"]), "measured hbm_gbs (MEASURED_PEAKS.json)"
+    return 6400.0, "fallback 6.4 TB/s"
+
+
 def _workload(name):
     return {"ising_large": wl.ising_large, "blume_capel_large": wl.blume_capel_large,
             "ising_small": wl.ising_quench_small,
@@ -607,6 +618,25 @@ def single_lattice(args, w, rank, world, stream, rates, sms, with_corr):
     ms_each = a_ev.elapsed_time(b_ev) / n_each
     lat.read_records(with_sums=False)
 
+    # the record pass alone: it reads the lattice once (plus the sums it
+    # writes), so its bound is the copy bandwidth
+    rec_ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    torch.cuda.synchronize()
+    rec_ev[0].record(stream)
+    for k in range(5):
+        lat.record()
+        rec_ev[k + 1].record(stream)
+    torch.cuda.synchronize()
+    rec_ms = statistics.median(rec_ev[k].elapsed_time(rec_ev[k + 1]) for k in range(5))
+    lat.read_records(with_sums=False)
+    rec_bytes = P.Lattice.nbytes(w.model, w.L) + 8 * w.L
+    hbm, hbm_src = _hbm_peak()
+    record = {"ms": rec_ms, "bytes": rec_bytes, "GB_per_s": rec_bytes / rec_ms / 1e6,
+              "peak_GB_per_s": hbm, "peak_basis": hbm_src, "frac": rec_bytes / rec_ms / 1e6 / hbm,
+              "kernel": "k_measure_stream" if w.L % 16384 == 0 else "k_measure",
+              "basis": "lattice bytes read once + row and column sums written, per record "
+                       "(median of 5, CUDA events, each after a slot clear)"}
+
     # end to end through the C ABI: host beta in, host record out, xi_2 on host
     # (per call: `every` sweeps with their betas from a host array, the
     # record read back to host arrays)
@@ -660,7 +690,7 @@ def single_lattice(args, w, rank, world, stream, rates, sms, with_corr):
         "record_every_sweep": {"ms_per_step": ms_each, "value": weak_each, "unit": UNIT,
                                "steps": n_each,
                                "overhead_vs_value": value / weak_each - 1.0},
-        "clocks": clk, "xi2_last": xi, "correlation": corr,
+        "clocks": clk, "xi2_last": xi, "correlation": corr, "record": record,
     }
 
 
@@ -692,7 +722,8 @@ def run_ours(args, w):
             "dtype": "int32", "data": "synthetic (hot-start lattice from the seeded Philox)",
             "config": main["config"], "roofline": main["roofline"], "e2e": main["e2e"],
             "gpu_launches": main["gpu_launches"],
-            "record_every_sweep": main["record_every_sweep"], "clocks": main["clocks"],
+            "record_every_sweep": main["record_every_sweep"], "record": main["record"],
+            "clocks": main["clocks"],
             "xi2_last": main["xi2_last"], "correlation": main["correlation"],
             "calibration": rates,
         }
