@@ -449,14 +449,81 @@ __device__ __forceinline__ void cc_zero(ColumnCounter &k)
         k.high[l] = 0;
 }
 
+// Blume-Capel column counter of s + 1 in {0, 1, 2}: per row a word of the
+// zero sites (weight 1) and a word of the +1 sites (weight 2), so that one
+// counter per column parity replaces separate +1 and -1 counters.  Levels
+// of weight 1 .. 32 in carry-save form; a carry of weight 64 leaves every
+// 16 rows into the bit-sliced high counter (a band's count is at most
+// 2 x 8192 = 64 x 256).
+constexpr int kHighBitsW = 9;
+struct WColumnCounter {
+    uint32_t l1, l2, l4, l8, l16, l32;
+    uint32_t high[kHighBitsW];
+    uint32_t e16, f32;  // pending carries of weight 16 and 32 inside a 16-row block
+};
+
+// Add one 4-row group: zero-site words z (weight 1) and +1-site words p
+// (weight 2); g = group index within the 16-row block (0..3).
+__device__ __forceinline__ void wcc_add4(WColumnCounter &k, const uint32_t (&z)[4], const uint32_t (&p)[4], int g)
+{
+    uint32_t a, b, c1, c2, c3, d1, e;
+    csa(k.l1, z[0], z[1], a);
+    csa(k.l1, z[2], z[3], b);
+    csa(k.l2, a, b, c1);
+    csa(k.l2, p[0], p[1], c2);
+    csa(k.l2, p[2], p[3], c3);
+    csa(k.l4, c1, c2, d1);
+    const uint32_t d2 = k.l4 & c3;
+    k.l4 ^= c3;
+    csa(k.l8, d1, d2, e);
+    if ((g & 1) == 0) {
+        k.e16 = e;
+        return;
+    }
+    uint32_t f;
+    csa(k.l16, k.e16, e, f);
+    if (g == 1) {
+        k.f32 = f;
+        return;
+    }
+    uint32_t c64;
+    csa(k.l32, k.f32, f, c64);
+#pragma unroll
+    for (int l = 0; l < kHighBitsW; ++l) {
+        const uint32_t c = k.high[l] & c64;
+        k.high[l] ^= c64;
+        c64 = c;
+    }
+}
+
+__device__ __forceinline__ int wcc_get(const WColumnCounter &k, int bit)
+{
+    int v = (int)((k.l1 >> bit) & 1u) + 2 * (int)((k.l2 >> bit) & 1u) + 4 * (int)((k.l4 >> bit) & 1u) +
+            8 * (int)((k.l8 >> bit) & 1u) + 16 * (int)((k.l16 >> bit) & 1u) + 32 * (int)((k.l32 >> bit) & 1u);
+    int h = 0;
+#pragma unroll
+    for (int l = 0; l < kHighBitsW; ++l)
+        h |= (int)((k.high[l] >> bit) & 1u) << l;
+    return v + 64 * h;
+}
+
+__device__ __forceinline__ void wcc_zero(WColumnCounter &k)
+{
+    k.l1 = k.l2 = k.l4 = k.l8 = k.l16 = k.l32 = k.e16 = k.f32 = 0;
+#pragma unroll
+    for (int l = 0; l < kHighBitsW; ++l)
+        k.high[l] = 0;
+}
+
 // The running state of one thread's walk down its word column: the
 // accumulators, the colour-0 rows above (U) and beside (S) the current
-// colour-1 row, and the column counters (even / odd columns, +1 and, for
-// Blume-Capel, -1 sites).
+// colour-1 row, and the column counters of the even / odd columns (Ising:
+// +1 sites; Blume-Capel: s + 1).
 struct MeasureState {
     int accB, accM, accQ;
     uint32_t Up, Sp, Un, Sn;
-    ColumnCounter ce_p, co_p, ce_m, co_m;
+    ColumnCounter ce_p, co_p;   // Ising
+    WColumnCounter ce_w, co_w;  // Blume-Capel
 };
 
 template <int MODEL>
@@ -464,11 +531,12 @@ __device__ __forceinline__ void measure_init(MeasureState &m)
 {
     m.accB = m.accM = m.accQ = 0;
     m.Up = m.Sp = m.Un = m.Sn = 0;
-    cc_zero(m.ce_p);
-    cc_zero(m.co_p);
-    if (MODEL == 1) {
-        cc_zero(m.ce_m);
-        cc_zero(m.co_m);
+    if (MODEL == 0) {
+        cc_zero(m.ce_p);
+        cc_zero(m.co_p);
+    } else {
+        wcc_zero(m.ce_w);
+        wcc_zero(m.co_w);
     }
 }
 
@@ -495,7 +563,7 @@ __device__ __forceinline__ void measure_group(MeasureState &m, const uint32_t (&
                                               const uint32_t (&Tn)[4], const uint32_t (&Dn)[4],
                                               const uint32_t (&En)[4], bool active, int (&raw)[4], int g)
 {
-    uint32_t evp[4], odp[4], evm[4], odm[4];
+    uint32_t evp[4], odp[4], evz[4], odz[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
         const bool odd = r & 1;
@@ -516,16 +584,15 @@ __device__ __forceinline__ void measure_group(MeasureState &m, const uint32_t (&
                 const uint32_t both = Tn_ & nb[k];
                 m.accB += __popc(both) - 2 * __popc(both & (Tp_ ^ pb[k]));
             }
-            const uint32_t plus1 = Tn_ & Tp_, minus1 = Tn_ & ~Tp_;
-            const uint32_t plus0 = m.Sn & m.Sp, minus0 = m.Sn & ~m.Sp;
+            const uint32_t plus1 = Tn_ & Tp_, plus0 = m.Sn & m.Sp;
             // (+1) - (-1) = 2 (+1) - (occupied); the occupied count is Q's
             const int occ = __popc(Tn_) + __popc(m.Sn);
             m.accQ += occ;
             raw[r] = active ? 64 + 2 * (__popc(plus1) + __popc(plus0)) - occ : 64;
             evp[r] = odd ? plus1 : plus0;
             odp[r] = odd ? plus0 : plus1;
-            evm[r] = odd ? minus1 : minus0;
-            odm[r] = odd ? minus0 : minus1;
+            evz[r] = odd ? ~Tn_ : ~m.Sn;  // zero sites
+            odz[r] = odd ? ~m.Sn : ~Tn_;
             m.Un = m.Sn;
             m.Sn = Dn[r];
         }
@@ -533,11 +600,12 @@ __device__ __forceinline__ void measure_group(MeasureState &m, const uint32_t (&
         m.Up = m.Sp;
         m.Sp = Dp[r];
     }
-    cc_add4(m.ce_p, evp[0], evp[1], evp[2], evp[3], g);
-    cc_add4(m.co_p, odp[0], odp[1], odp[2], odp[3], g);
-    if (MODEL == 1) {
-        cc_add4(m.ce_m, evm[0], evm[1], evm[2], evm[3], g);
-        cc_add4(m.co_m, odm[0], odm[1], odm[2], odm[3], g);
+    if (MODEL == 0) {
+        cc_add4(m.ce_p, evp[0], evp[1], evp[2], evp[3], g);
+        cc_add4(m.co_p, odp[0], odp[1], odp[2], odp[3], g);
+    } else {
+        wcc_add4(m.ce_w, evz, evp, g);
+        wcc_add4(m.co_w, odz, odp, g);
     }
 }
 
@@ -569,9 +637,9 @@ __device__ __forceinline__ void measure_finish(MeasureState &m, bool active, int
             if (MODEL == 0) {
                 ve = 2 * cc_get(m.ce_p, b) - rows;
                 vo = 2 * cc_get(m.co_p, b) - rows;
-            } else {
-                ve = cc_get(m.ce_p, b) - cc_get(m.ce_m, b);
-                vo = cc_get(m.co_p, b) - cc_get(m.co_m, b);
+            } else {  // the counters hold the sum of s + 1
+                ve = wcc_get(m.ce_w, b) - rows;
+                vo = wcc_get(m.co_w, b) - rows;
             }
             if (ve)
                 atomicAdd(&C[xe], ve);
@@ -733,7 +801,7 @@ constexpr uint64_t kStreamWaitNs = 2000000000ull;
 template <int MODEL>
 struct StreamShape {
     static constexpr int kPlanes = MODEL == 0 ? 1 : 2;   // sign (and occupancy) planes per colour
-    static constexpr int kStages = MODEL == 0 ? 8 : 4;
+    static constexpr int kStages = MODEL == 0 ? 8 : 4;  // 66.6 KB of stages either way
     // per plane: the 4 colour-1 rows, then the 4 colour-0 rows below them
     // (the layouts of the two tiled boxes; every block 128-byte aligned)
     static constexpr int kPlaneWords = 4 * (kStreamSeg + kStreamRowD);
@@ -850,7 +918,7 @@ __device__ void stream_produce(uint32_t sbase, uint32_t full0, uint32_t empty0, 
 }
 
 template <int MODEL>
-__global__ void __launch_bounds__(kStreamThreads, MODEL == 0 ? 3 : 2)
+__global__ void __launch_bounds__(kStreamThreads, 3)  // 3 blocks per SM: 71 / 72 registers
     k_measure_stream(Planes pl, int H, int64_t *__restrict__ rec_hdr, int32_t *__restrict__ R,
                      int32_t *__restrict__ C, int64_t sweep, uint32_t tx_extra,
                      const __grid_constant__ CUtensorMap tmT, const __grid_constant__ CUtensorMap tmD, int tmap)
