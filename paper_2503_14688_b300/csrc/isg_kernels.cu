@@ -385,7 +385,7 @@ __global__ void __launch_bounds__(kBcThreads, kBcMinBlocks)
 // ---------------------------------------------------------------------------
 constexpr int kMeasureBand = 8192;  // rows per band at most
 // blocks per SM the launch bounds ask for, per model
-constexpr int kMeasureBlocksIsing = 3, kMeasureBlocksBc = 2;
+constexpr int kMeasureBlocksIsing = 3, kMeasureBlocksBc = 3;  // 80 registers each
 constexpr int kHighBits = 10;       // high counter: multiples of 16 up to 16 * 1023
 
 struct ColumnCounter {
