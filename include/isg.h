@@ -338,7 +338,10 @@ isg_status isg_ensemble_get_tuning(const isg_ensemble *ens, isg_ensemble_tuning 
  * budget and the slot count allow, and advances every running request by
  * chunk_sweeps sweeps -- lattices that fit in shared memory (Ising L <= 1280,
  * Blume-Capel L <= 896) together in one persistent launch, larger ones on
- * streams of their own, overlapping it.  A result does not depend on what
+ * streams of their own, overlapping it.  Those streams carry priorities by
+ * size (the largest lattices the least; the internal main stream the
+ * greatest), so that mid-size requests' launches are scheduled ahead of the
+ * largest ones' remaining blocks.  A result does not depend on what
  * else ran or where chunks were cut (per-site keying).  Requests leave the
  * schedule when done, when cancelled, when their deadline passes, or when
  * their allocation or a launch fails; each outcome is a state of

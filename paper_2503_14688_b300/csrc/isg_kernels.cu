@@ -774,23 +774,23 @@ __global__ void __launch_bounds__(kMeasureThreads, MODEL == 0 ? kMeasureBlocksIs
 // ---------------------------------------------------------------------------
 // The record pass with its rows streamed into shared memory by the copy
 // engine (k_measure_stream): the walk and arithmetic of k_measure
-// (measure_group / measure_finish), for lattices whose rows split into whole
-// segments of kStreamSeg words (L a multiple of 16384).  A block has one
-// consumer thread per word of its segment (8 warps) and one producer warp,
-// whose lane 0 copies 4-row groups into a ring of shared-memory stages,
-// completing on the stage's `full` mbarrier: per plane one tiled copy of a
-// 4-row box through a tensor map of the planes (away from the row ends and
-// the periodic wrap), else one 1D bulk copy per row.  Consumer
-// warps release a stage through its `empty` mbarrier, and the producer then
-// adds that group's row sums to R before it refills the stage: each warp
-// leaves the warp sums of the group's four raw row values, two rows to a
-// word (16-bit halves), in shared memory.  Per row a stage holds the colour-1 target segment and
-// the colour-0 row below it with kStreamHalo words on each side: the side
-// neighbours of the segment's edge words, taken from the row's other end at
-// the periodic wrap.  Every wait is bounded (kStreamWaitNs); one that runs
-// out marks the record failed (sweep field INT64_MIN, read by the host as
-// ISG_ERR_DEVICE_TIMEOUT), and the producer waits (bounded) for its copies
-// in flight before the block returns.
+// (measure_group / measure_finish), for lattices whose rows split into
+// whole segments of kStreamSeg words (L a multiple of 16384).  A block has
+// one consumer thread per word of its segment (8 warps) and one producer
+// warp, whose lane 0 copies 4-row groups into a ring of shared-memory
+// stages, completing on the stage's `full` mbarrier: per plane one tiled
+// copy of a 4-row box through a tensor map of the planes (away from the
+// row ends and the periodic wrap), else one 1D bulk copy per row.  Per row
+// a stage holds the colour-1 target segment and the colour-0 row below it
+// with kStreamHalo words on each side: the side neighbours of the
+// segment's edge words, taken from the row's other end at the periodic
+// wrap.  Consumer warps release a stage through its `empty` mbarrier; each
+// leaves the warp sums of the group's four raw row values in shared memory,
+// two rows to a word (16-bit halves), and the producer adds them to R
+// before it refills the stage.  Every wait is bounded (kStreamWaitNs); one
+// that runs out marks the record failed (sweep field INT64_MIN, read by the
+// host as ISG_ERR_DEVICE_TIMEOUT), and the producer waits (bounded) for its
+// copies in flight before the block returns.
 // ---------------------------------------------------------------------------
 constexpr int kStreamSeg = 256;   // words per segment: one consumer thread each
 constexpr int kStreamHalo = 4;    // 16 bytes, the bulk-copy granule

@@ -93,6 +93,7 @@ struct Request {
     int64_t rec_cap = 0;      // periodic records
     int64_t rec_read = 0;     // periodic records already read by the caller
     cudaStream_t stream = nullptr;  // own stream (large requests)
+    int32_t stream_prio = 0;        // its priority (smaller lattices: higher)
     cudaEvent_t done = nullptr;
     // large requests: events after their last two chunks; a chunk is queued
     // only once the one two before it has finished, so at most two chunks
@@ -124,7 +125,10 @@ struct isg_server {
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
     std::deque<uint64_t> queue;      // arrival order
     std::vector<uint64_t> active;    // admitted, not finished
-    std::vector<cudaStream_t> free_streams;
+    // idle request streams by priority; priorities run from prio_least
+    // (largest lattices) to prio_greatest (numerically lower)
+    std::map<int32_t, std::vector<cudaStream_t>> free_streams;
+    int32_t prio_least = 0, prio_greatest = 0;
     std::vector<int32_t> free_final_slots;
     int64_t *h_finals = nullptr;     // pinned, 4 int64 per slot (max_active slots)
     // double-buffered launch buffers of the batch kernel (one set per round parity)
@@ -161,7 +165,7 @@ void release_device(isg_server *s, Request &r)
     if (r.planes) cudaFreeAsync(r.planes, st);
     if (r.recs) cudaFreeAsync(r.recs, st);
     if (r.stream)
-        s->free_streams.push_back(r.stream);
+        s->free_streams[r.stream_prio].push_back(r.stream);
     r.planes = nullptr;
     r.recs = nullptr;
     r.stream = nullptr;
@@ -174,14 +178,33 @@ size_t request_bytes(const Request &r)
     return isg_lattice_bytes(r.model, r.L) + record_stride(r.L) * (size_t)(r.rec_cap + 1);
 }
 
+// Stream priority of a large request: the lattices of 2^28 sites or more
+// (L = 16384) take the least priority and every halving of L one step more,
+// so that the short launches of mid-size requests are scheduled ahead of
+// the remaining blocks of the largest ones (the batch of small requests
+// runs at the greatest priority).  Scheduling only: results do not depend
+// on it.
+int32_t request_priority(const isg_server *s, const Request &r)
+{
+    int steps = 0;
+    for (int64_t l = r.L; l < 16384 && steps < 30; l *= 2)
+        ++steps;
+    const int32_t p = s->prio_least - steps;  // greater priority = numerically lower
+    const int32_t floor_p = std::min(s->prio_greatest + 1, s->prio_least);  // the batch keeps the greatest
+    return std::max(p, floor_p);
+}
+
 isg_status admit(isg_server *s, Request &r)
 {
     if (!r.small) {
-        if (!s->free_streams.empty()) {
-            r.stream = s->free_streams.back();
-            s->free_streams.pop_back();
+        r.stream_prio = request_priority(s, r);
+        std::vector<cudaStream_t> &pool = s->free_streams[r.stream_prio];
+        if (!pool.empty()) {
+            r.stream = pool.back();
+            pool.pop_back();
         } else {
-            SCUDA(cudaStreamCreateWithFlags(&r.stream, cudaStreamNonBlocking), "request stream");
+            SCUDA(cudaStreamCreateWithPriority(&r.stream, cudaStreamNonBlocking, r.stream_prio),
+                  "request stream");
         }
     }
     cudaStream_t st = req_stream(s, r);
@@ -482,10 +505,14 @@ isg_status isg_server_create(const isg_server_desc *d, isg_server **out)
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
     s->budget = std::min(d->hbm_budget, free_b);
+    if (cudaDeviceGetStreamPriorityRange(&s->prio_least, &s->prio_greatest) != cudaSuccess) {
+        cudaGetLastError();
+        s->prio_least = s->prio_greatest = 0;
+    }
     if (d->stream) {
         s->stream = (cudaStream_t)d->stream;
     } else {
-        if (cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess)
+        if (cudaStreamCreateWithPriority(&s->stream, cudaStreamNonBlocking, s->prio_greatest) != cudaSuccess)
             return cleanup(scuda(cudaGetLastError(), "stream"));
         s->own_stream = true;
     }
@@ -541,8 +568,9 @@ void isg_server_destroy(isg_server *s)
             if (ev) cudaEventDestroy(ev);
     }
     cudaDeviceSynchronize();
-    for (cudaStream_t st : s->free_streams)
-        cudaStreamDestroy(st);
+    for (auto &kv : s->free_streams)
+        for (cudaStream_t st : kv.second)
+            cudaStreamDestroy(st);
     if (s->d_counter) cudaFree(s->d_counter);
     if (s->h_finals) cudaFreeHost(s->h_finals);
     for (int k = 0; k < 2; ++k) {
