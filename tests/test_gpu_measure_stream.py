@@ -6,8 +6,10 @@ side words of a segment's edges come from the row's other end there -- and
 the register-walk record of the same lattice held as row slabs with four
 segments per row (inner segments, halos from the neighbour segments).  A
 wait that runs out (ISG_INJECT_WAIT: one block is promised 16 bytes that
-never come) must fail that record with ISG_ERR_DEVICE_TIMEOUT, the next
-record must be right, and no device fault is involved."""
+never come) must fail that record with ISG_ERR_DEVICE_TIMEOUT -- through the
+lattice calls, a served request's final record and the allocation-free
+entry point -- the next record must be right, and no device fault is
+involved."""
 import numpy as np
 import pytest
 
@@ -111,6 +113,57 @@ def test_a_wait_that_runs_out_fails_only_its_record(isg, model):
         assert len(rest) == 1
         _same(rest[0], good)
         assert np.array_equal(lat.get(), s)
+    finally:
+        isg.lattice.inject_fault(3, 0)
+        lat.close()
+
+
+def test_a_failed_final_record_fails_only_its_request(isg):
+    """A served request of L = 16384 runs on its own stream and ends with a
+    streamed record pass; when that pass's waits run out the request ends
+    ISG_REQ_FAILED with ISG_ERR_DEVICE_TIMEOUT, and the next one is done."""
+    srv = isg.Server(hbm_budget=2 << 30, max_active=2, chunk_sweeps=10)
+    try:
+        isg.lattice.inject_fault(3, 1)
+        bad = srv.submit(0, 16384, 11, 10, [0], [0.44])
+        srv.drain()
+        r = srv.poll(bad)
+        assert r.state == 5 and r.error == -4
+        good = srv.submit(0, 16384, 12, 10, [0], [0.44], keep=True)
+        srv.drain()
+        r = srv.poll(good)
+        assert r.state == 2 and r.sweeps_done == 10
+        lat = isg.Lattice(16384, 0, seed=12)
+        lat.init_random()
+        lat.sweep(10, beta=0.44)
+        o = lat.measure()
+        lat.close()
+        assert (r.B, r.M, r.Q) == (o.B, o.M, o.Q)
+        srv.release(good)
+    finally:
+        isg.lattice.inject_fault(3, 0)
+        srv.close()
+
+
+def test_a_wait_that_runs_out_in_the_noalloc_pass(isg):
+    """isg_measure_planes_noalloc at L = 16384 takes the streamed pass: a
+    wait that runs out is reported as ISG_ERR_DEVICE_TIMEOUT and the next
+    call is right."""
+    import torch
+
+    from paper_2503_14688_b300 import _abi
+
+    L = 16384
+    buf = torch.empty(isg.Lattice.nbytes(0, L), dtype=torch.uint8, device="cuda")
+    lat = isg.Lattice(L, 0, seed=13, device_buf=buf)
+    try:
+        lat.init_random()
+        want = lat.measure()
+        isg.lattice.inject_fault(3, 1)
+        with pytest.raises(_abi.IsgError) as e:
+            isg.measure_planes_noalloc(0, L, buf)
+        assert e.value.status == -4
+        _same(isg.measure_planes_noalloc(0, L, buf), want)
     finally:
         isg.lattice.inject_fault(3, 0)
         lat.close()
