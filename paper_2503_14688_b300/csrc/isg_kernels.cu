@@ -1613,25 +1613,28 @@ cudaError_t launch_measure(const Planes &pl, void *record, int64_t sweep, cudaSt
     const dim3 grid((unsigned)bx, (unsigned)((pl.L + H - 1) / H));
     if (pl.W % kStreamSeg == 0 && (reinterpret_cast<uintptr_t>(pl.base) & 15u) == 0) {
         // whole segments (and the 16-byte aligned planes bulk copies need):
-        // the streamed pass, on the same grid, one segment per block
-        const uint32_t extra = injected_wait_failure() ? 16u : 0u;
-        CUtensorMap tmT, tmD;
-        const int tmap = stream_tensor_maps(pl, &tmT, &tmD) ? 1 : 0;
-        cudaError_t e;
-        if (pl.model == 0) {
-            e = cudaFuncSetAttribute(k_measure_stream<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)StreamShape<0>::kSmem);
-            if (e == cudaSuccess)
+        // the streamed pass, on the same grid, one segment per block; if its
+        // shared memory cannot be had, the register walk below (same sums)
+        const cudaError_t ea = pl.model == 0
+                                   ? cudaFuncSetAttribute(k_measure_stream<0>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)StreamShape<0>::kSmem)
+                                   : cudaFuncSetAttribute(k_measure_stream<1>,
+                                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                          (int)StreamShape<1>::kSmem);
+        if (ea == cudaSuccess) {
+            const uint32_t extra = injected_wait_failure() ? 16u : 0u;
+            CUtensorMap tmT, tmD;
+            const int tmap = stream_tensor_maps(pl, &tmT, &tmD) ? 1 : 0;
+            if (pl.model == 0)
                 k_measure_stream<0><<<grid, kStreamThreads, StreamShape<0>::kSmem, st>>>(
                     pl, (int)H, hdr, R, C, sweep, extra, tmT, tmD, tmap);
-        } else {
-            e = cudaFuncSetAttribute(k_measure_stream<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)StreamShape<1>::kSmem);
-            if (e == cudaSuccess)
+            else
                 k_measure_stream<1><<<grid, kStreamThreads, StreamShape<1>::kSmem, st>>>(
                     pl, (int)H, hdr, R, C, sweep, extra, tmT, tmD, tmap);
+            return cudaGetLastError();
         }
-        return e != cudaSuccess ? e : cudaGetLastError();
+        cudaGetLastError();
     }
     if (pl.model == 0)
         k_measure<0><<<grid, kMeasureThreads, 0, st>>>(pl, (int)H, hdr, R, C, sweep);
