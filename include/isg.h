@@ -182,14 +182,18 @@ isg_status isg_record(isg_lattice *lat);
 
 /* Move up to max pending records, oldest first, into out[0..]: the scalars,
  * and the row/column sums into the host arrays each out[i] points to (if not
- * NULL).  *count = records moved.  Synchronises. */
+ * NULL).  *count = records moved.  Synchronises.  A record whose pass ran
+ * out of time (a bounded wait of the streamed record pass gave up) is
+ * dropped from the ring and the call returns ISG_ERR_DEVICE_TIMEOUT with
+ * *count = the records moved before it. */
 isg_status isg_read_records(isg_lattice *lat, isg_obs *out, int64_t max, int64_t *count);
 
 /* Number of records waiting in the ring. */
 isg_status isg_pending_records(const isg_lattice *lat, int64_t *count);
 
 /* Observables of the current lattice into *out (host arrays).  Does not touch
- * the record ring.  Synchronises. */
+ * the record ring.  Synchronises.  ISG_ERR_DEVICE_TIMEOUT if the record
+ * pass ran out of time (a bounded wait gave up; see ISG_INJECT_WAIT). */
 isg_status isg_measure(isg_lattice *lat, isg_obs *out);
 
 /* Largest L accepted by isg_measure_planes_noalloc. */
@@ -412,7 +416,8 @@ isg_status isg_server_cancel(isg_server *srv, uint64_t id);
 /* Rounds until every submitted request is done (waits for arrivals). */
 isg_status isg_server_drain(isg_server *srv);
 isg_status isg_server_poll(isg_server *srv, uint64_t id, isg_result *out);
-/* Periodic records of a finished, kept request (as isg_read_records). */
+/* Periodic records of a finished, kept request (as isg_read_records; a
+ * failed record is passed over and reported as ISG_ERR_DEVICE_TIMEOUT). */
 isg_status isg_server_read_records(isg_server *srv, uint64_t id, isg_obs *out, int64_t max,
                                    int64_t *count);
 /* Final lattice of a finished, kept request (L*L host bytes).  Synchronises. */
