@@ -1183,6 +1183,50 @@ __device__ __forceinline__ int pair_sum(uint32_t an, uint32_t ap, uint32_t bn, u
     return __popc(both) - 2 * __popc(both & (ap ^ bp));
 }
 
+// Ising rows y_s .. y_s + n - 1 of one band segment in which the vertical
+// partner row y + r does not wrap: own words at own + i W, the partner
+// plane's rows at hrow + i W, the vertical partners at vrow + i W.  Rows of
+// even i (the parity of y_s) take the horizontal partner words (a0, b0)
+// shifted by s0, rows of odd i (a1, b1, s1).  Adds the differing vertical
+// pairs to mv and the differing horizontal pairs to mh.  Four rows per
+// step with all their loads issued first and their parity known at
+// compile time.
+__device__ __forceinline__ void corr_ising_rows(const uint32_t *own, const uint32_t *hrow, const uint32_t *vrow,
+                                                int n, int64_t W, int64_t a0, int64_t b0, unsigned s0,
+                                                int64_t a1, int64_t b1, unsigned s1, int &mv, int &mh)
+{
+    int i = 0;
+#pragma unroll 1
+    for (; i + 4 <= n; i += 4) {
+        uint32_t A[4], V[4], H1[4], H2[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            A[j] = __ldg(own + j * W);
+            V[j] = __ldg(vrow + j * W);
+            H1[j] = __ldg(hrow + j * W + ((j & 1) ? a1 : a0));
+            H2[j] = __ldg(hrow + j * W + ((j & 1) ? b1 : b0));
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            mv += __popc(A[j] ^ V[j]);
+            mh += __popc(A[j] ^ __funnelshift_r(H1[j], H2[j], (j & 1) ? s1 : s0));
+        }
+        own += 4 * W;
+        hrow += 4 * W;
+        vrow += 4 * W;
+    }
+    for (; i < n; ++i) {
+        const bool odd = i & 1;
+        const uint32_t a = __ldg(own);
+        mv += __popc(a ^ __ldg(vrow));
+        mh += __popc(a ^ __funnelshift_r(__ldg(hrow + (odd ? a1 : a0)), __ldg(hrow + (odd ? b1 : b0)),
+                                         odd ? s1 : s0));
+        own += W;
+        hrow += W;
+        vrow += W;
+    }
+}
+
 template <int MODEL>
 __global__ void __launch_bounds__(kMeasureThreads)
     k_correlation(Planes pl, int H, int nr, const int64_t *__restrict__ rlist,
@@ -1205,9 +1249,9 @@ __global__ void __launch_bounds__(kMeasureThreads)
         const int cp = c ^ (int)(r & 1);
         int ax = 0, ay = 0;
         if (active && MODEL == 0) {
-            // Ising (the MODEL == 1 terms below compile away).  Horizontal
-            // partner of row parity q = (c ^ y) & 1: bits i + kk of the same
-            // row of plane cp, i.e. two words w1, w2 shifted by sh
+            // Ising.  Horizontal partner of row parity q = (c ^ y) & 1: bits
+            // i + kk of the same row of plane cp, i.e. two words w1, w2
+            // shifted by sh
             auto split = [&](int q, int64_t &a, int64_t &b, unsigned &sh) {
                 int64_t kk = (r & 1) ? (r - 1) / 2 + q : r / 2;
                 if (kk >= half)
@@ -1222,62 +1266,25 @@ __global__ void __launch_bounds__(kMeasureThreads)
             unsigned oe, oo;
             split(0, w1e, w2e, oe);
             split(1, w1o, w2o, oo);
-            // row pointers: own row y, vertical partner row y + r (periodic),
-            // partner plane's row y; advanced by one row per step
-            const int64_t dn = occ(c) - sgn(c), dpn = occ(cp) - sgn(cp);  // occupancy planes
-            const uint32_t *arow = sgn(c) + y0 * W + w;
-            const uint32_t *hrow = sgn(cp) + y0 * W;
-            int64_t yv = y0 + r;
-            if (yv >= L)
-                yv -= L;
-            const uint32_t *vrow = sgn(cp) + yv * W + w;
-            const uint32_t *vend = sgn(cp) + LW;  // one past the partner plane
-            int64_t y = y0;
-            // four rows per step, all loads issued before any is used (8.5%
-            // faster at L = 2^20); the band's remaining rows one at a time
-            for (; y + 4 <= y1; y += 4) {
-                uint32_t A[4], V[4], H1[4], H2[4];
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool q = (c ^ (int)(y + j)) & 1;
-                    A[j] = __ldg(arow + j * W);
-                    const uint32_t *vr = vrow + j * W;
-                    if (vr >= vend)
-                        vr -= LW;
-                    V[j] = __ldg(vr);
-                    H1[j] = __ldg(hrow + j * W + (q ? w1o : w1e));
-                    H2[j] = __ldg(hrow + j * W + (q ? w2o : w2e));
-                }
-#pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const bool q = (c ^ (int)(y + j)) & 1;
-                    ay += pair_sum<MODEL>(0u, A[j], 0u, V[j]);
-                    ax += pair_sum<MODEL>(0u, A[j], 0u, __funnelshift_r(H1[j], H2[j], q ? oo : oe));
-                }
-                arow += 4 * W;
-                hrow += 4 * W;
-                vrow += 4 * W;
-                if (vrow >= vend)
-                    vrow -= LW;
+            // the band in at most two segments, split where the vertical
+            // partner row y + r wraps to y + r - L, so that no row checks
+            const int64_t y_wrap = L - r;
+            int mv = 0, mh = 0, rows = 0;  // differing vertical / horizontal pairs, rows walked
+#pragma unroll 1
+            for (int sgm = 0; sgm < 2; ++sgm) {
+                const int64_t ys = sgm == 0 ? y0 : (y0 > y_wrap ? y0 : y_wrap);
+                const int64_t ye = sgm == 0 ? (y1 < y_wrap ? y1 : y_wrap) : y1;
+                if (ye <= ys)
+                    continue;
+                const bool p = (c ^ (int)ys) & 1;  // parity of the segment's first row
+                corr_ising_rows(sgn(c) + ys * W + w, sgn(cp) + ys * W, sgn(cp) + (ys + r - (sgm ? L : 0)) * W + w,
+                                (int)(ye - ys), W, p ? w1o : w1e, p ? w2o : w2e, p ? oo : oe, p ? w1e : w1o,
+                                p ? w2e : w2o, p ? oe : oo, mv, mh);
+                rows += (int)(ye - ys);
             }
-            for (; y < y1; ++y) {
-                const uint32_t a_p = __ldg(arow);
-                const uint32_t a_n = MODEL == 1 ? __ldg(arow + dn) : 0u;
-                const uint32_t v_p = __ldg(vrow);
-                const uint32_t v_n = MODEL == 1 ? __ldg(vrow + dpn) : 0u;
-                ay += pair_sum<MODEL>(a_n, a_p, v_n, v_p);
-                const bool q = (c ^ (int)y) & 1;
-                const uint32_t *h1 = hrow + (q ? w1o : w1e), *h2 = hrow + (q ? w2o : w2e);
-                const unsigned sh = q ? oo : oe;
-                const uint32_t h_p = __funnelshift_r(__ldg(h1), __ldg(h2), sh);
-                const uint32_t h_n = MODEL == 1 ? __funnelshift_r(__ldg(h1 + dpn), __ldg(h2 + dpn), sh) : 0u;
-                ax += pair_sum<MODEL>(a_n, a_p, h_n, h_p);
-                arow += W;
-                hrow += W;
-                vrow += W;
-                if (vrow >= vend)
-                    vrow -= LW;
-            }
+            // 32 pairs per row and axis: s s' = 1 - 2 [bits differ]
+            ax = 32 * rows - 2 * mh;
+            ay = 32 * rows - 2 * mv;
         } else if (active) {
             // Blume-Capel: the same sums with 64-bit row products; the row
             // pointers of the Ising path took it from 40 to 128 registers and
