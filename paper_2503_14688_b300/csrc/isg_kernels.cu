@@ -1174,11 +1174,9 @@ __global__ void k_slab_convert(SlabPlanes sp, int8_t *s, int to_planes, int32_t 
 // A pair contributes s s' = 1 - 2 [bits differ] (Ising) or
 // n n' (1 - 2 (p ^ p')) (Blume-Capel), counted with popcounts.
 // ---------------------------------------------------------------------------
-template <int MODEL>
-__device__ __forceinline__ int pair_sum(uint32_t an, uint32_t ap, uint32_t bn, uint32_t bp)
+// A Blume-Capel word pair: sum of n n' (1 - 2 (p ^ p')) over its 32 sites.
+__device__ __forceinline__ int bc_pair_sum(uint32_t an, uint32_t ap, uint32_t bn, uint32_t bp)
 {
-    if (MODEL == 0)
-        return 32 - 2 * __popc(ap ^ bp);
     const uint32_t both = an & bn;
     return __popc(both) - 2 * __popc(both & (ap ^ bp));
 }
@@ -1269,7 +1267,7 @@ __global__ void __launch_bounds__(kMeasureThreads)
             // the band in at most two segments, split where the vertical
             // partner row y + r wraps to y + r - L, so that no row checks
             const int64_t y_wrap = L - r;
-            int mv = 0, mh = 0, rows = 0;  // differing vertical / horizontal pairs, rows walked
+            int rows = 0, mv = 0, mh = 0;  // rows walked; differing vertical / horizontal pairs
 #pragma unroll 1
             for (int sgm = 0; sgm < 2; ++sgm) {
                 const int64_t ys = sgm == 0 ? y0 : (y0 > y_wrap ? y0 : y_wrap);
@@ -1277,18 +1275,21 @@ __global__ void __launch_bounds__(kMeasureThreads)
                 if (ye <= ys)
                     continue;
                 const bool p = (c ^ (int)ys) & 1;  // parity of the segment's first row
-                corr_ising_rows(sgn(c) + ys * W + w, sgn(cp) + ys * W, sgn(cp) + (ys + r - (sgm ? L : 0)) * W + w,
-                                (int)(ye - ys), W, p ? w1o : w1e, p ? w2o : w2e, p ? oo : oe, p ? w1e : w1o,
+                const uint32_t *own = sgn(c) + ys * W + w, *hr = sgn(cp) + ys * W;
+                const uint32_t *vr = sgn(cp) + (ys + r - (sgm ? L : 0)) * W + w;
+                const int n = (int)(ye - ys);
+                corr_ising_rows(own, hr, vr, n, W, p ? w1o : w1e, p ? w2o : w2e, p ? oo : oe, p ? w1e : w1o,
                                 p ? w2e : w2o, p ? oe : oo, mv, mh);
-                rows += (int)(ye - ys);
+                rows += n;
             }
             // 32 pairs per row and axis: s s' = 1 - 2 [bits differ]
             ax = 32 * rows - 2 * mh;
             ay = 32 * rows - 2 * mv;
         } else if (active) {
-            // Blume-Capel: the same sums with 64-bit row products; the row
-            // pointers of the Ising path took it from 40 to 128 registers and
-            // made it 24% slower
+            // Blume-Capel: per-row 64-bit row products (row pointers took it
+            // from 40 to 128 registers and made it 24% slower; the Ising
+            // walk's segments and four-row steps made it 10% slower at
+            // L = 2^19, where it is nearer the memory bound)
             const uint32_t *os = sgn(c), *on = occ(c), *ps = sgn(cp), *pn = occ(cp);
             for (int64_t y = y0; y < y1; ++y) {
                 const uint32_t a_p = __ldg(os + y * W + w);
@@ -1299,7 +1300,7 @@ __global__ void __launch_bounds__(kMeasureThreads)
                     yv -= L;
                 const uint32_t v_p = __ldg(ps + yv * W + w);
                 const uint32_t v_n = MODEL == 1 ? __ldg(pn + yv * W + w) : 0u;
-                ay += pair_sum<MODEL>(a_n, a_p, v_n, v_p);
+                ay += bc_pair_sum(a_n, a_p, v_n, v_p);
                 // horizontal partner: bits i + kk of row y of plane cp
                 int64_t kk = (r & 1) ? (r - 1) / 2 + ((c ^ (int)y) & 1) : r / 2;
                 if (kk >= half)
@@ -1313,7 +1314,7 @@ __global__ void __launch_bounds__(kMeasureThreads)
                 const uint32_t h_n = MODEL == 1
                                          ? __funnelshift_r(__ldg(pn + y * W + w1), __ldg(pn + y * W + w2), o)
                                          : 0u;
-                ax += pair_sum<MODEL>(a_n, a_p, h_n, h_p);
+                ax += bc_pair_sum(a_n, a_p, h_n, h_p);
             }
         }
         long long sx = __reduce_add_sync(0xFFFFFFFFu, ax);
