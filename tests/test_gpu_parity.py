@@ -260,3 +260,28 @@ def test_correlation_matches_oracle(isg, orc, model, L):
     assert np.array_equal(gx, ox) and np.array_equal(gy, oy)
     o = lat.measure()
     assert gx[r.index(1)] + gy[r.index(1)] == o.B and gx[0] == o.Q
+
+
+@pytest.mark.parametrize("model", [0, 1])
+@pytest.mark.parametrize("L", [2112, 16384])
+def test_correlation_matches_oracle_with_many_bands(isg, orc, model, L):
+    """The correlation pass where a launch has many row bands (1-row bands
+    at L = 2112, 16-row bands of four 4-row steps at L = 16384), so that
+    the vertical partner row wraps inside bands for most distances (the
+    band is walked in two segments there) and segments start on rows of
+    either parity; seeded lattices with a bias, since the sums of a hot
+    start are near zero."""
+    rng = np.random.default_rng(wl.BASE_SEED + 820 + L + model)
+    if model == 0:
+        s = np.where(rng.random((L, L)) < 0.6, 1, -1).astype(np.int8)
+    else:
+        s = rng.choice(np.array([-1, 0, 1], dtype=np.int8), size=(L, L), p=[0.25, 0.25, 0.5])
+    lat = isg.Lattice(L, model, seed=1)
+    try:
+        lat.set(s)
+        r = sorted(set([0, 1, 2, 3, 5, 7, 64, 65, 1001, L // 2 - 1, L // 2, L // 2 + 1, L - 3, L - 1]))
+        gx, gy = lat.correlation(r)
+    finally:
+        lat.close()
+    ox, oy = orc.correlation(s, r)
+    assert np.array_equal(gx, ox) and np.array_equal(gy, oy)
