@@ -977,8 +977,11 @@ __global__ void __launch_bounds__(kStreamThreads, 3)  // 3 blocks per SM: 71 / 7
 #pragma unroll
         for (int g = 0; g < 4; ++g) {
             const int s = gb % S::kStages + g;
-            if (!mbar_wait(full0 + 8u * s, parity, kStreamWaitNs)) {
-                mark_record_failed(rec_hdr);
+            // the warp gives up as one (its lanes meet in warp reductions below)
+            const bool landed = mbar_wait(full0 + 8u * s, parity, kStreamWaitNs);
+            if (__any_sync(0xFFFFFFFFu, !landed)) {
+                if (lane == 0)
+                    mark_record_failed(rec_hdr);
                 return;
             }
             const uint32_t *st = smem + s * S::kStageWords;
